@@ -1,0 +1,86 @@
+"""Pins of the oracle's iaf_psc_exp integration and ring-buffer delivery (no GPU)."""
+import math
+
+import numpy as np
+
+from oracle import neuron as on
+from paper_2512_09502_gb300 import workloads as wl
+
+
+def _one_neuron_net(params, drives=()):
+    return wl.Network("one", [wl.Population(1, params)], [], list(drives))
+
+
+def test_psp_closed_form_on_grid():
+    """A current jump J at step 0 gives V(k h) equal to the closed-form PSP."""
+    p = wl.BALANCED_PARAMS
+    net = _one_neuron_net(p)
+    sim = on.Simulator(net, np.array([0, 0]), np.zeros(0, np.int64), np.zeros(0, np.int64),
+                       np.zeros(0), 8)
+    J = 87.8
+    sim.ring[0, 0, 0] = J         # arrives in step 0
+    _, vs = sim.run(60, record_v=True)
+    t = np.arange(60) * net.dt    # after step k the neuron has integrated k steps
+    ref = on.psp_closed_form(J, p, t)
+    np.testing.assert_allclose(vs[:, 0], ref, rtol=0, atol=1e-12)
+    assert vs[:, 0].max() > 0.1
+
+
+def test_steady_state_and_isi_closed_form():
+    p = wl.NeuronParams(tau_m=10.0, C_m=250.0, I_e=600.0, V_th=20.0, V_reset=10.0, t_ref=2.0)
+    net = _one_neuron_net(p)
+    sim = on.Simulator(net, np.array([0, 0]), np.zeros(0, np.int64), np.zeros(0, np.int64),
+                       np.zeros(0), 8)
+    spikes, vs = sim.run(3000, record_v=True)
+    v_inf = p.I_e * p.tau_m / p.C_m             # 24 mV > V_th
+    h = net.dt
+    # first spike: first n with V_inf (1 - e^{-n h / tau_m}) >= V_th
+    n1 = next(n for n in range(1, 10000) if v_inf * (1 - math.exp(-n * h / p.tau_m)) >= p.V_th)
+    assert spikes[0][0] == n1 - 1               # step index n1-1 completes n1 integrations
+    k = next(n for n in range(1, 10000)
+             if v_inf + (p.V_reset - v_inf) * math.exp(-n * h / p.tau_m) >= p.V_th)
+    isi = np.diff([s for s, _ in spikes])
+    assert np.all(isi == 20 + k)
+    # sub-threshold steady state
+    p2 = wl.NeuronParams(I_e=300.0, V_th=1e9)
+    sim2 = on.Simulator(_one_neuron_net(p2), np.array([0, 0]), np.zeros(0, np.int64),
+                        np.zeros(0, np.int64), np.zeros(0), 8)
+    _, vs2 = sim2.run(2000, record_v=True)
+    n = np.arange(1, 2001)
+    ref = 300.0 * 10.0 / 250.0 * (1 - np.exp(-n * h / 10.0))
+    np.testing.assert_allclose(vs2[:, 0], ref, rtol=0, atol=1e-12)
+
+
+def test_tau_syn_equal_tau_m_limit():
+    h = 0.1
+    a = on.propagators(wl.NeuronParams(tau_m=10.0, tau_syn_ex=10.0, tau_syn_in=10.0), h)
+    b = on.propagators(wl.NeuronParams(tau_m=10.0, tau_syn_ex=10.0 * (1 + 1e-9),
+                                       tau_syn_in=10.0 * (1 + 1e-9)), h)
+    assert abs(a["P21_ex"] - b["P21_ex"]) < 1e-12 * a["P21_ex"] * 1e3
+    # closed form of the limit: (h / C_m) e^{-h/tau_m}
+    assert abs(a["P21_ex"] - h / 250.0 * math.exp(-h / 10.0)) < 1e-18
+
+
+def test_refractory_clamp():
+    p = wl.NeuronParams(I_e=2000.0, t_ref=2.0)
+    net = _one_neuron_net(p)
+    sim = on.Simulator(net, np.array([0, 0]), np.zeros(0, np.int64), np.zeros(0, np.int64),
+                       np.zeros(0), 8)
+    spikes, vs = sim.run(200, record_v=True)
+    s0 = spikes[0][0]
+    assert np.all(vs[s0:s0 + 21, 0] == p.V_reset)       # spike step + 20 refractory steps
+    assert vs[s0 + 21, 0] > p.V_reset
+
+
+def test_delivery_slot_and_receptor():
+    net = wl.Network("two", [wl.Population(2, wl.NeuronParams(V_th=1e9))], [], [])
+    rp = np.array([0, 2, 2])
+    tgt = np.array([1, 1])
+    d = np.array([3, 5])
+    w = np.array([10.0, -4.0])
+    sim = on.Simulator(net, rp, tgt, d, w, 8)
+    sim.step_no = 6
+    sim.deliver(6, [0])
+    assert sim.ring[(6 + 3) % 8, 0, 1] == 10.0
+    assert sim.ring[(6 + 5) % 8, 1, 1] == -4.0
+    assert np.count_nonzero(sim.ring) == 2
