@@ -1,0 +1,231 @@
+/*
+ * snn.h -- C ABI of the GB300-native on-device network construction and spike
+ * delivery library (libsnn.so).
+ *
+ * The library follows the problem statement of "Scalable Construction of Spiking
+ * Neural Networks using up to thousands of GPUs" (arXiv 2512.09502):
+ *   - create neuron populations (Results, introduction of the phases: "neuron and
+ *     device creation");
+ *   - connect them with probabilistic rules (Methods, "Creation of the remote
+ *     connection structures for point-to-point MPI communication": Connect /
+ *     RemoteConnect(sigma, s, tau, t, p, C, D, alpha));
+ *   - calibrate = network construction + "simulation preparation" (Methods,
+ *     "Simulation phases and optimization");
+ *   - simulate (state propagation), read spikes.
+ * The paper's MPI ranks become logical ranks inside one GPU: neurons are distributed
+ * round-robin over n_ranks partitions, each rank stores the connections of its
+ * targets with image neurons for remote sources, and spikes are routed through the
+ * paper's point-to-point (R/L, S, T/P) or collective (H, I, G/Q) maps held in device
+ * memory.
+ *
+ * Conventions for every call:
+ *   - returns SNN_OK (0) or a negative SNN_E* status; no exception crosses the ABI;
+ *     snn_last_error() gives a message for the last failing call on a context;
+ *   - pointers named host_* are host memory owned by the caller; the library copies
+ *     into / out of them and synchronises its stream before returning;
+ *   - all device memory is owned by the library and comes from the snn_allocator
+ *     given at snn_create (or cudaMallocAsync / cudaFreeAsync when it is NULL);
+ *   - all device work is issued on the stream given at snn_create;
+ *   - global neuron ids (gids) are 0-based in creation order; rank-local indices
+ *     appear only in snn_get_connections / snn_get_row / snn_get_maps.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SNN_OK 0
+#define SNN_EINVAL (-1)    /* invalid argument or unsupported combination        */
+#define SNN_ENOMEM (-2)    /* the allocator returned NULL                        */
+#define SNN_ECUDA (-3)     /* a CUDA runtime call or kernel failed               */
+#define SNN_ETIMEOUT (-4)  /* a bounded device-side wait gave up                 */
+#define SNN_ESTATE (-5)    /* call not valid in the current phase                */
+#define SNN_EOVERFLOW (-6) /* a caller buffer or the spike log was too small     */
+
+/* ---- enums --------------------------------------------------------------- */
+#define SNN_RULE_FIXED_INDEGREE 0     /* param = K: K sources per target            */
+#define SNN_RULE_FIXED_TOTAL 1        /* param = N: N (source, target) draws        */
+#define SNN_RULE_PAIRWISE_BERNOULLI 2 /* param = p: each pair kept with prob. p    */
+
+#define SNN_W_CONST 0        /* weight = mean                                          */
+#define SNN_W_NORMAL_SIGN 1  /* normal(mean, sd), clamped at 0 to keep mean's sign    */
+#define SNN_D_CONST 0        /* delay = mean ms, rounded to steps, >= 1 step          */
+#define SNN_D_NORMAL_MIN 1   /* normal(mean, sd) ms clipped below at lo, quantised    */
+
+#define SNN_WEIGHT_F32 0   /* stored weights: fp32                                    */
+#define SNN_WEIGHT_BF16 1  /* bf16 (round to nearest even of the fp32 draw)           */
+#define SNN_WEIGHT_F16 2   /* fp16 of w / scale, scale = power of two per source row  */
+
+#define SNN_EXCHANGE_P2P 0        /* route spikes through T/P packets and L maps  */
+#define SNN_EXCHANGE_COLLECTIVE 1 /* route through Q positions and I arrays       */
+
+/* map selectors for snn_get_maps (paper notation) */
+#define SNN_MAP_R 0  /* R_{tau,sigma}: remote source local index, ascending (on tau) */
+#define SNN_MAP_L 1  /* L_{tau,sigma}: image local index, aligned with R (on tau)    */
+#define SNN_MAP_S 2  /* S_{tau,sigma}: source sequence built on sigma (== R)         */
+#define SNN_MAP_T 3  /* T_{sigma,s} for every s of sigma, concatenated (CSR values) */
+#define SNN_MAP_P 4  /* P_{sigma,s} aligned with T                                   */
+#define SNN_MAP_TP_PTR 5 /* CSR offsets of T/P over s = 0..M_sigma (M_sigma+1)       */
+#define SNN_MAP_H 6  /* H_{0,sigma}: sorted sources of sigma with a remote image     */
+#define SNN_MAP_I 7  /* I_{0,sigma,tau}: image of H[j] in tau or -1                  */
+#define SNN_MAP_Q 8  /* Q_{sigma,s} (group 0 only): position of s in H, CSR values   */
+#define SNN_MAP_GQ_PTR 9 /* CSR offsets of G/Q over s = 0..M_sigma                   */
+
+/* ---- structs ------------------------------------------------------------- */
+typedef struct snn_ctx snn_ctx;
+
+typedef struct snn_allocator {
+  /* Return device memory of at least `bytes` bytes usable on `stream`, or NULL. */
+  void* (*alloc)(void* user, size_t bytes, void* stream);
+  /* Release memory obtained from alloc. */
+  void (*free)(void* user, void* ptr, size_t bytes, void* stream);
+  void* user;
+} snn_allocator;
+
+typedef struct snn_config {
+  double dt_ms;                /* simulation resolution h in ms (> 0)                 */
+  uint32_t n_ranks;            /* logical ranks (>= 1), neurons round-robin            */
+  int32_t weight_format;       /* SNN_WEIGHT_*                                         */
+  int32_t exchange;            /* SNN_EXCHANGE_* (used when n_ranks > 1)               */
+  int32_t use_graph;           /* capture the simulation step as a CUDA graph          */
+  uint64_t spike_log_capacity; /* spikes kept for snn_get_spikes; 0 = no recording    */
+  int32_t radix_bits;          /* sort digit width 8..11; 0 = tuned default            */
+  int32_t device;              /* CUDA device ordinal                                  */
+} snn_config;
+
+/* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in
+ * ms, currents in pA.  V0 = V_init_lo, or uniform in [lo, hi) from the VINIT stream
+ * when V_init_hi > V_init_lo. */
+typedef struct snn_iaf_psc_exp_params {
+  double tau_m, C_m, tau_syn_ex, tau_syn_in, V_th, V_reset, t_ref, I_e;
+  double V_init_lo, V_init_hi;
+  uint64_t v_init_seed;
+} snn_iaf_psc_exp_params;
+
+typedef struct snn_rule {
+  int32_t kind;  /* SNN_RULE_* */
+  double param;  /* K, N or p */
+} snn_rule;
+
+typedef struct snn_dist {
+  int32_t kind;  /* SNN_W_* for weights, SNN_D_* for delays */
+  double mean, sd, lo;
+} snn_dist;
+
+typedef struct snn_stats_t {
+  uint64_t n_neurons, n_synapses, n_images, n_blocks, n_projections;
+  uint64_t n_spikes, n_events, steps_done;   /* since calibrate                 */
+  uint64_t device_bytes, peak_device_bytes;  /* through the allocator            */
+  uint64_t spike_log_overflow;               /* spikes dropped by a full log    */
+  double t_generate_ms, t_sort_ms, t_finalize_ms, t_maps_ms, t_calibrate_ms;
+  double t_simulate_ms;
+  uint32_t sort_passes, radix_bits, key_bits, ring_slots;
+  uint32_t gen_kernel_launches, sort_kernel_launches;
+} snn_stats_t;
+
+/* ---- lifecycle -----------------------------------------------------------
+ * snn_create: new context on config->device; `alloc` may be NULL (cudaMallocAsync);
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  EINVAL on a bad
+ * config.  The context owns every device buffer; snn_destroy frees them. */
+int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_stream,
+               snn_ctx** out);
+void snn_destroy(snn_ctx* ctx);
+const char* snn_last_error(snn_ctx* ctx);
+
+/* ---- construction (before snn_calibrate; ESTATE afterwards) -------------- */
+
+/* Neuron creation ("neuron and device creation" phase): appends n neurons; writes
+ * the first new gid to *first_gid. */
+int snn_create_population(snn_ctx* ctx, uint32_t n, const snn_iaf_psc_exp_params* params,
+                          uint32_t* first_gid);
+
+/* Connect: sources [src_first, src_first + n_src) onto targets [tgt_first,
+ * tgt_first + n_tgt) (global ids) with `rule`, weights from `weight` (pA), delays from
+ * `delay` (ms).  Multapses and autapses are allowed (fixed in-degree / fixed total),
+ * as in the paper's balanced network.  Draws come from Philox-4x32-10 keyed by
+ * `seed` and counted per projection, so the network does not depend on n_ranks
+ * (the paper's aligned RNG_{sigma,tau} streams, Methods "Point-to-point MPI
+ * communication").  Writes the projection id (call order) to *proj_id.  The build is
+ * deferred to snn_calibrate so that every projection and rank is built in one batch. */
+int snn_connect(snn_ctx* ctx, uint32_t src_first, uint32_t n_src, uint32_t tgt_first,
+                uint32_t n_tgt, const snn_rule* rule, const snn_dist* weight,
+                const snn_dist* delay, uint64_t seed, uint32_t* proj_id);
+
+/* RemoteConnect(sigma, s, tau, t, p, C, D, alpha) on contiguous rank-local index
+ * ranges: sources s_first..s_first+n_s-1 of rank sigma onto targets
+ * t_first..t_first+n_t-1 of rank tau (round-robin partition, so the gids are
+ * s * n_ranks + sigma: a strided projection of the same generator).  Port p must be
+ * 0; alpha is -1 (point-to-point) or 0 (the all-ranks group) -- the maps of both
+ * exchange schemes are always built.  EINVAL for ranks or ranges out of bounds. */
+int snn_remote_connect(snn_ctx* ctx, uint32_t sigma, uint32_t s_first, uint32_t n_s,
+                       uint32_t tau, uint32_t t_first, uint32_t n_t, uint32_t port,
+                       const snn_rule* rule, const snn_dist* weight, const snn_dist* delay,
+                       int32_t group, uint64_t seed, uint32_t* proj_id);
+
+/* Independent Poisson drive of rate_hz for gids [first, first + n): each input spike
+ * adds weight_pA to the synaptic current of the sign's receptor. */
+int snn_set_poisson_drive(snn_ctx* ctx, uint32_t first, uint32_t n, double rate_hz,
+                          double weight_pA, uint64_t seed);
+
+/* Network construction and simulation preparation on the GPU: connection
+ * generation, source/delay sort, per-rank CSR, image neurons and every map, neuron
+ * state and propagators (FP64 on the host, stored FP32).  ETIMEOUT if a bounded
+ * device wait gave up, ENOMEM / ECUDA as usual.  Call once. */
+int snn_calibrate(snn_ctx* ctx);
+
+/* ---- simulation ---------------------------------------------------------- */
+
+/* Advance `steps` steps of dt (state propagation): neuron update, spike routing
+ * through the maps, ring-buffer delivery.  Returns after the work is queued and the
+ * stream synchronised. */
+int snn_simulate(snn_ctx* ctx, uint32_t steps);
+
+/* Copy recorded spikes (step, gid), sorted by (step, gid), into host arrays of
+ * capacity `cap`; *n_out = number recorded.  EOVERFLOW if cap is too small (the
+ * first cap spikes are written). */
+int snn_get_spikes(snn_ctx* ctx, uint32_t* host_step, uint32_t* host_gid, uint64_t cap,
+                   uint64_t* n_out);
+
+/* Copy V (mV), I_ex, I_in (pA) of gids [first, first + n) into host arrays (any may be
+ * NULL). */
+int snn_get_state(snn_ctx* ctx, uint32_t first, uint32_t n, float* host_V, float* host_Iex,
+                  float* host_Iin);
+
+/* ---- inspection (parity tests) ------------------------------------------ */
+
+/* Rank `rank`'s connections: row_ptr over its M_rank local rows then its image rows
+ * (n_rows + 1 entries, relative to the rank's first synapse), targets as rank-local
+ * indices, weights as fp32 (decoded from the stored format), delays in steps.  Any
+ * output may be NULL to query sizes only (*n_rows, *n_syn).  EOVERFLOW when a
+ * capacity is too small. */
+int snn_get_connections(snn_ctx* ctx, uint32_t rank, uint64_t* host_row_ptr,
+                        uint64_t row_cap, uint32_t* host_tgt, float* host_w,
+                        uint8_t* host_d, uint64_t syn_cap, uint64_t* n_rows,
+                        uint64_t* n_syn);
+
+/* One row of rank `rank` (sampled parity at full size). */
+int snn_get_row(snn_ctx* ctx, uint32_t rank, uint64_t row, uint32_t* host_tgt, float* host_w,
+                uint8_t* host_d, uint64_t cap, uint64_t* n_out);
+
+/* One map (SNN_MAP_*) as int64 values; tau / sigma as in the paper's notation
+ * (tau = rank holding the map for R/L/I, sigma = source rank; T/P/H/Q/ptr use
+ * sigma only). */
+int snn_get_maps(snn_ctx* ctx, uint32_t tau, uint32_t sigma, int32_t which, int64_t* host_buf,
+                 uint64_t cap, uint64_t* n_out);
+
+/* Integer CDF table of a projection's quantised-normal delay (thresholds, s_min). */
+int snn_get_delay_table(snn_ctx* ctx, uint32_t proj_id, uint32_t* host_thr, uint64_t cap,
+                        uint64_t* n_out, uint32_t* s_min);
+
+int snn_stats(snn_ctx* ctx, snn_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNN_H */

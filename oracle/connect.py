@@ -14,7 +14,10 @@ Readings (the paper does not fix the generator):
   is the projection-local counter:
     - fixed in-degree K:   c = (t - t_first) * K + k, for target t, k < K;
     - fixed total N:       c = j, the draw index;
-    - pairwise Bernoulli:  c = q = (t - t_first) * n_src + (s - s_first).
+    - pairwise Bernoulli:  c = q = i_t * n_src + i_s.
+  Sources and targets are the projection's i-th members src_first + i * src_stride
+  and tgt_first + i * tgt_stride (stride 1 for population ranges; a rank-local range
+  of a round-robin partition has stride R).
 * Words of the SYNAPSE block: w0 -> source index, w1 -> delay step, (w2, w3) ->
   weight.  A fixed-total draw takes its target from w0 of the FT_TARGET block.  A
   Bernoulli pair q is kept iff word (q & 3) of the PB_TEST block at counter q >> 2 is
@@ -76,15 +79,15 @@ def projection_synapses(net, pid: int, counters=None):
         c = np.arange(pr.n_tgt * K, dtype=np.uint64) if counters is None else np.asarray(counters, np.uint64)
         t_local = (c // np.uint64(K)).astype(np.int64)
         b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
-        src = pr.src_first + sm.uniform_index(b[0], pr.n_src).astype(np.int64)
-        tgt = pr.tgt_first + t_local
+        src = pr.src_first + pr.src_stride * sm.uniform_index(b[0], pr.n_src).astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * t_local
     elif kind == "fixed_total":
         N = int(pr.rule.param)
         c = np.arange(N, dtype=np.uint64) if counters is None else np.asarray(counters, np.uint64)
         b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
         bt = ph.stream(c, pid, ph.PURPOSE_FT_TARGET, pr.seed)
-        src = pr.src_first + sm.uniform_index(b[0], pr.n_src).astype(np.int64)
-        tgt = pr.tgt_first + sm.uniform_index(bt[0], pr.n_tgt).astype(np.int64)
+        src = pr.src_first + pr.src_stride * sm.uniform_index(b[0], pr.n_src).astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * sm.uniform_index(bt[0], pr.n_tgt).astype(np.int64)
     elif kind == "pairwise_bernoulli":
         assert counters is None
         q = np.arange(pr.n_tgt * pr.n_src, dtype=np.uint64)
@@ -94,8 +97,8 @@ def projection_synapses(net, pid: int, counters=None):
         keep = word < np.uint64(bernoulli_threshold(pr.rule.param))
         c = q[keep]
         b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
-        src = pr.src_first + (c % np.uint64(pr.n_src)).astype(np.int64)
-        tgt = pr.tgt_first + (c // np.uint64(pr.n_src)).astype(np.int64)
+        src = pr.src_first + pr.src_stride * (c % np.uint64(pr.n_src)).astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * (c // np.uint64(pr.n_src)).astype(np.int64)
     else:
         raise ValueError(kind)
     d = sm.delay_steps(pr.delay, net.dt, b[1], len(c))
@@ -123,7 +126,8 @@ def fixed_indegree_target(net, pid: int, t: int):
     parity at sizes the full oracle cannot build)."""
     pr = net.projections[pid]
     K = int(pr.rule.param)
-    c = np.arange((t - pr.tgt_first) * K, (t - pr.tgt_first + 1) * K, dtype=np.uint64)
+    i = (t - pr.tgt_first) // pr.tgt_stride
+    c = np.arange(i * K, (i + 1) * K, dtype=np.uint64)
     return projection_synapses(net, pid, counters=c)
 
 

@@ -1,0 +1,436 @@
+// build.cu -- on-device network construction: connection generation, the
+// source/delay radix sort, and the final per-rank CSR layout.
+//
+// Paper: Methods, "Creation of the remote connection structures for point-to-point
+// MPI communication" (connections generated in GPU memory from the rule dictionary,
+// sorted by source), "GPU memory levels" (sorted by source as first key so that one
+// source's connections are (first index, count)).  The per-rank structure (targets on
+// their rank, remote sources as image rows) follows "Remote connections".
+//
+// Pipeline (one launch each, every projection and every logical rank batched):
+//   gen_kernel       counter-based generation of all records, written in generation
+//                    order into their rank segment, with the digit histograms of every
+//                    sort pass accumulated on the fly (no extra read of the records);
+//   bin_scan_kernel  exclusive scan of the histograms -> global bin bases;
+//   onesweep_pass    one stable LSD pass per digit: warp-level multisplit ranking,
+//                    decoupled look-back over tiles (bounded spin), shared-memory
+//                    staging so that each digit run is written contiguously;
+//   finalize_kernel  decodes the sorted records: rank-local target, weight
+//                    (regenerated from the counter), delay; writes the SoA arrays and
+//                    the dense row starts (the CSR) from record boundaries.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "snn_internal.cuh"
+
+namespace snn {
+
+constexpr int GEN_BLOCK = 256;
+constexpr int GEN_TILE = 4096;
+constexpr int SORT_BLOCK = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
+constexpr int MAX_PASSES = 6;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+uint32_t sort_tile_items(uint32_t) { return SORT_TILE; }
+
+// ---------------------------------------------------------------------------
+// generation
+// ---------------------------------------------------------------------------
+template <int RB>
+__global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
+  constexpr int BINS = 1 << RB;
+  __shared__ uint32_t s_hist[MAX_PASSES][BINS];
+  __shared__ uint32_t s_tbl[256];
+  __shared__ DevBlock s_blk;
+  __shared__ DevProj s_proj;
+  const int tid = threadIdx.x;
+  const Geom g = a.g;
+  const uint32_t passes = a.passes;
+  for (int i = tid; i < MAX_PASSES * BINS; i += GEN_BLOCK) (&s_hist[0][0])[i] = 0;
+
+  const uint64_t per = (a.n_gen_tiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * per;
+  const uint64_t t1 = min(t0 + per, a.n_gen_tiles);
+  int cur_rank = -1;
+  const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
+
+  for (uint64_t tile = t0; tile < t1; ++tile) {
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t lo = 0, hi = a.nblocks;   // last block with tile_first <= tile
+      while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a.blocks[mid].tile_first <= tile) lo = mid + 1; else hi = mid;
+      }
+      s_blk = a.blocks[lo - 1];
+      s_proj = a.projs[s_blk.proj];
+    }
+    __syncthreads();
+    const DevBlock blk = s_blk;
+    const DevProj& P = s_proj;
+    if ((int)blk.rank != cur_rank) {          // flush the previous segment's histogram
+      if (cur_rank >= 0) {
+        for (int i = tid; i < (int)passes * BINS; i += GEN_BLOCK) {
+          const uint32_t v = (&s_hist[0][0])[i];
+          if (v) atomicAdd((unsigned long long*)&a.hist[((uint64_t)cur_rank * passes) * BINS + i], v);
+          (&s_hist[0][0])[i] = 0;
+        }
+      }
+      cur_rank = blk.rank;
+    }
+    if (P.d_kind == 1)
+      for (uint32_t i = tid; i < P.d_tbl_len; i += GEN_BLOCK) s_tbl[i] = a.dtables[P.d_tbl_off + i];
+    __syncthreads();
+
+    const uint64_t e0 = (tile - blk.tile_first) * (uint64_t)GEN_TILE;
+    const uint32_t n = (uint32_t)min((uint64_t)GEN_TILE, blk.count - e0);
+    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    for (uint32_t i = tid; i < n; i += GEN_BLOCK) {
+      const uint64_t e = e0 + i;
+      uint64_t c;
+      if (P.rule == kRuleFixedIndegree) {
+        const uint64_t m = div_magic(e, P.K, P.magic_div);
+        const uint64_t k = e - m * P.K;
+        c = ((uint64_t)blk.ti0 + m * blk.tstep) * P.K + k;
+      } else {
+        c = e;   // fixed total on one rank: draws in order
+      }
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id,
+                                               kPurposeSynapse), key);
+      const uint32_t src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
+      uint32_t sig = 0, s = src;
+      if (g.R > 1) {
+        s = (uint32_t)div_magic(src, g.R, g.magic_R);
+        sig = src - s * g.R;
+      }
+      const uint32_t slot = sig == blk.rank ? 0u : (sig < blk.rank ? sig + 1 : sig);
+      uint32_t d = P.d_const;
+      if (P.d_kind == 1) d += upper_bound_u32(s_tbl, P.d_tbl_len, b.y);
+      const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
+      a.rec_a[blk.out_base + e] = (kk << g.cbits) | ((P.cbase + c) & cmask);
+#pragma unroll
+      for (int p = 0; p < MAX_PASSES; ++p)
+        if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  if (cur_rank >= 0) {
+    for (int i = tid; i < (int)passes * BINS; i += GEN_BLOCK) {
+      const uint32_t v = (&s_hist[0][0])[i];
+      if (v) atomicAdd((unsigned long long*)&a.hist[((uint64_t)cur_rank * passes) * BINS + i], v);
+    }
+  }
+}
+
+cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st) {
+  if (a.n_gen_tiles == 0) return cudaSuccess;
+  const uint64_t grid = std::min<uint64_t>(a.n_gen_tiles, (uint64_t)a.num_sms * 8);
+  if (a.radix_bits != 8) return cudaErrorInvalidValue;
+  gen_kernel<8><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// histogram scan -> bin bases (absolute positions)
+// ---------------------------------------------------------------------------
+__global__ void bin_scan_kernel(const uint64_t* hist, uint64_t* base, const uint64_t* seg_start,
+                                uint32_t R, uint32_t passes, uint32_t bins) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= R * passes) return;
+  const uint32_t r = i / passes;
+  uint64_t acc = seg_start[r];
+  for (uint32_t b = 0; b < bins; ++b) {
+    base[(uint64_t)i * bins + b] = acc;
+    acc += hist[(uint64_t)i * bins + b];
+  }
+}
+
+cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st) {
+  const uint32_t n = a.g.R * a.passes;
+  if (n == 0) return cudaSuccess;
+  bin_scan_kernel<<<(n + 127) / 128, 128, 0, st>>>(a.hist, a.bin_base, a.seg_start, a.g.R, a.passes,
+                                                  1u << a.radix_bits);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// one stable LSD pass (onesweep: Adinets & Merrill 2022)
+// ---------------------------------------------------------------------------
+constexpr uint64_t ST_AGG = 1ull << 62;
+constexpr uint64_t ST_INC = 2ull << 62;
+constexpr uint64_t ST_VAL = (1ull << 46) - 1;
+
+__device__ __forceinline__ uint64_t ld_status(const uint64_t* p) {
+  return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
+  *(volatile unsigned long long*)p = v;
+}
+
+template <int RB>
+__global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_t pass,
+                                                             const uint64_t* __restrict__ in,
+                                                             uint64_t* __restrict__ out,
+                                                             uint32_t epoch) {
+  constexpr int BINS = 1 << RB;
+  constexpr int NW = SORT_BLOCK / 32;
+  constexpr int BPT = BINS >= SORT_BLOCK ? BINS / SORT_BLOCK : 1;   // bins per thread
+  __shared__ uint32_t s_whist[NW][BINS];
+  __shared__ uint64_t s_stage[SORT_TILE];
+  __shared__ uint32_t s_binstart[BINS];
+  __shared__ uint64_t s_gbase[BINS];
+  __shared__ uint32_t s_wsum[NW];
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) s_tile = atomicAdd(&a.counters[pass], 1u);
+  for (int i = tid; i < NW * BINS; i += SORT_BLOCK) (&s_whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint64_t tile = s_tile;
+  if (tile >= a.n_sort_tiles) return;
+
+  // segment of this tile
+  uint32_t lo = 0, hi = a.g.R;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a.seg_tile0[mid] <= tile) lo = mid + 1; else hi = mid;
+  }
+  const uint32_t seg = lo - 1;
+  const uint64_t tile_in_seg = tile - a.seg_tile0[seg];
+  const uint64_t base = a.seg_start[seg] + tile_in_seg * SORT_TILE;
+  const uint32_t n = (uint32_t)min((uint64_t)SORT_TILE, a.seg_start[seg + 1] - base);
+  const uint32_t shift = a.g.cbits + pass * RB;
+  const uint32_t dbits = min((uint32_t)RB, a.g.key_bits - pass * RB);
+  const uint64_t dmask = (1ull << dbits) - 1;
+
+  uint64_t rec[SORT_ITEMS];
+  uint32_t dig[SORT_ITEMS];
+  uint32_t rnk[SORT_ITEMS];
+  const uint32_t wbase = warp * 32 * SORT_ITEMS;
+#pragma unroll
+  for (int j = 0; j < SORT_ITEMS; ++j) {
+    const uint32_t idx = wbase + j * 32 + lane;
+    if (idx < n) {
+      rec[j] = in[base + idx];
+      dig[j] = (uint32_t)((rec[j] >> shift) & dmask);
+    } else {
+      rec[j] = 0;
+      dig[j] = BINS;   // padding: ranked among itself, never placed
+    }
+  }
+  const uint32_t lt = (1u << lane) - 1;
+#pragma unroll
+  for (int j = 0; j < SORT_ITEMS; ++j) {
+    const uint32_t d = dig[j];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && d < BINS) {
+      old = s_whist[warp][d];
+      s_whist[warp][d] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rnk[j] = old + __popc(peers & lt);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // per bin: exclusive prefix over warps, tile count, look-back, global base
+  uint32_t tot[BPT];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int q = 0; q < BPT; ++q) {
+    const int b = tid * BPT + q;
+    uint32_t t = 0;
+    if (b < BINS) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = s_whist[w][b];
+        s_whist[w][b] = t;
+        t += c;
+      }
+    }
+    tot[q] = t;
+    tsum += t;
+  }
+  const bool first = tile_in_seg == 0;
+  const uint64_t ep = (uint64_t)(epoch & 0xFFFF) << 46;
+  uint64_t* strow = a.status + tile * BINS;
+#pragma unroll
+  for (int q = 0; q < BPT; ++q) {
+    const int b = tid * BPT + q;
+    if (b < BINS) st_status(strow + b, (first ? ST_INC : ST_AGG) | ep | tot[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < BPT; ++q) {
+    const int b = tid * BPT + q;
+    if (b >= BINS) continue;
+    uint64_t excl = 0;
+    if (!first) {
+      uint64_t k = tile - 1;
+      while (true) {
+        const uint64_t* sp = a.status + k * BINS + b;
+        uint64_t s = ld_status(sp);
+        uint32_t spins = 0;
+        while (((s >> 62) == 0) || (((s >> 46) & 0xFFFF) != (epoch & 0xFFFF))) {
+          if (++spins > SPIN_LIMIT) {
+            atomicOr(a.err, kErrTimeout);
+            s = ST_INC | ep;
+            break;
+          }
+          __nanosleep(32);
+          s = ld_status(sp);
+        }
+        excl += s & ST_VAL;
+        if ((s >> 62) == 2) break;
+        --k;
+      }
+      st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
+    }
+    s_gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * BINS + b] + excl;
+  }
+
+  // tile-local exclusive scan of the bin counts (thread-contiguous bins)
+  uint32_t incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+  uint32_t run = woff + incl - tsum;
+#pragma unroll
+  for (int q = 0; q < BPT; ++q) {
+    const int b = tid * BPT + q;
+    if (b < BINS) s_binstart[b] = run;
+    run += tot[q];
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int j = 0; j < SORT_ITEMS; ++j) {
+    const uint32_t d = dig[j];
+    if (d < BINS) s_stage[s_binstart[d] + s_whist[warp][d] + rnk[j]] = rec[j];
+  }
+  __syncthreads();
+  const uint64_t seg_end = a.seg_start[seg + 1];
+  for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
+    const uint64_t r = s_stage[k];
+    const uint32_t d = (uint32_t)((r >> shift) & dmask);
+    const uint64_t gpos = s_gbase[d] + (k - s_binstart[d]);
+    if (gpos < seg_end) out[gpos] = r; else atomicOr(a.err, kErrBounds);
+  }
+}
+
+cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
+                             uint32_t epoch, cudaStream_t st) {
+  if (a.n_sort_tiles == 0) return cudaSuccess;
+  if (a.radix_bits != 8) return cudaErrorInvalidValue;
+  onesweep_pass<8><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, 0, st>>>(a, pass, in, out, epoch);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// finalize: SoA arrays + dense row starts
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float draw_weight(const DevProj& P, uint32_t w2, uint32_t w3) {
+  if (P.w_kind == 0) return P.w_mean;
+  const float u1 = u01(w2), u2 = u01(w3);
+  const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+  float w = fmaf(P.w_sd, z, P.w_mean);
+  return P.w_mean >= 0.f ? fmaxf(w, 0.f) : fminf(w, 0.f);
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64_t* __restrict__ rec,
+                                                      uint64_t E) {
+  const Geom g = a.g;
+  const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
+  const uint64_t smask = (1ull << g.sb) - 1;
+  const uint64_t dmask = (1ull << g.db) - 1;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
+    const uint32_t seg = g.R == 1 ? 0u : upper_bound_u64(a.seg_start + 1, g.R, i);
+    const uint64_t seg_lo = a.seg_start[seg], seg_hi = a.seg_start[seg + 1];
+    const uint64_t r = rec[i];
+    const uint64_t key = r >> g.cbits;
+    const uint64_t cidx = r & cmask;
+    const uint32_t d = (uint32_t)(key & dmask);
+    const uint32_t s = (uint32_t)((key >> g.db) & smask);
+    const uint32_t slot = (uint32_t)(key >> (g.db + g.sb));
+    const uint32_t* doff = a.dense_off + (uint64_t)seg * g.R;
+    const uint64_t row = (uint64_t)doff[slot] + s;
+    if (slot >= g.R || row >= g.N) {   // corrupt record: flag it, touch nothing
+      atomicOr(a.err, kErrBounds);
+      continue;
+    }
+    int64_t prow = -1;
+    if (i > seg_lo) {
+      const uint64_t kp = rec[i - 1] >> g.cbits;
+      prow = (int64_t)((uint64_t)doff[kp >> (g.db + g.sb)] + ((kp >> g.db) & smask));
+    }
+    uint64_t* dn = a.dense + (uint64_t)seg * ((uint64_t)g.N + 1);
+    for (int64_t x = prow + 1; x <= (int64_t)row; ++x) dn[x] = i;
+    if (i == seg_hi - 1)
+      for (uint64_t x = row + 1; x <= g.N; ++x) dn[x] = seg_hi;
+
+    // projection of the counter, then target and weight regenerated from it
+    const uint32_t p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
+    const DevProj& P = a.projs[p];
+    const uint64_t c = cidx - P.cbase;
+    uint32_t t;
+    if (P.rule == kRuleFixedIndegree) {
+      t = P.tgt_first + (uint32_t)div_magic(c, P.K, P.magic_div) * P.tgt_stride;
+    } else if (P.rule == kRuleFixedTotal) {
+      const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);
+      t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
+    } else {
+      t = P.tgt_first + (uint32_t)div_magic(c, P.n_src, P.magic_div) * P.tgt_stride;
+    }
+    const uint32_t tl = g.R == 1 ? t : (uint32_t)div_magic(t, g.R, g.magic_R);
+    const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
+    const float w = draw_weight(P, b.z, b.w);
+    a.tgt[i] = tl;
+    a.d[i] = (uint8_t)d;
+    if (a.w_format == 0) {
+      ((float*)a.w)[i] = w;
+    } else if (a.w_format == 1) {
+      ((__nv_bfloat16*)a.w)[i] = __float2bfloat16_rn(w);
+    } else {
+      uint32_t sig = 0, src_s = s;
+      if (slot != 0) sig = slot <= seg ? slot - 1 : slot; else sig = seg;
+      const uint64_t src_gid = (uint64_t)src_s * g.R + sig;
+      const float sc = a.row_scale_src ? a.row_scale_src[src_gid] : 1.0f;
+      ((__half*)a.w)[i] = __float2half_rn(w / sc);
+    }
+  }
+}
+
+__global__ void fill_empty_segments(uint64_t* dense, const uint64_t* seg_start, uint32_t R,
+                                    uint32_t N) {
+  const uint64_t total = (uint64_t)R * (N + 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t seg = (uint32_t)(i / (N + 1));
+    if (seg_start[seg] == seg_start[seg + 1]) dense[i] = seg_start[seg];
+  }
+}
+
+cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E, cudaStream_t st) {
+  const uint64_t total = (uint64_t)a.g.R * (a.g.N + 1);
+  fill_empty_segments<<<(unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)a.num_sms * 16), 256, 0,
+                        st>>>(a.dense, a.seg_start, a.g.R, a.g.N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || E == 0) return e;
+  const uint64_t grid = std::min<uint64_t>((E + 255) / 256, (uint64_t)a.num_sms * 16);
+  finalize_kernel<<<(unsigned)grid, 256, 0, st>>>(a, rec, E);
+  return cudaGetLastError();
+}
+
+}  // namespace snn

@@ -1,0 +1,32 @@
+// sim_internal.cuh -- device state of the simulation phase and its launchers.
+#pragma once
+#include "snn_internal.cuh"
+
+namespace snn {
+
+struct SimArgs {
+  uint32_t N, R;
+  float* V; float* Iex; float* Iin; uint16_t* refr;
+  const uint16_t* pop_of;      // population of each neuron position
+  const uint32_t* gid_of;      // gid of each neuron position (R > 1)
+  const DevPop* pops; uint32_t npops;
+  const DevDrive* drives; uint32_t ndrives;
+  const uint32_t* poisson_tbl; uint32_t poisson_tbl_len;
+  float* ring; uint32_t ring_mask;            // [D][2][N]
+  uint32_t* step;                             // device step counter
+  uint32_t* n_items; uint32_t* items;         // [2] counts, [2][N] per-step lists
+  unsigned long long* n_logged; uint2* log; unsigned long long log_cap;
+  unsigned long long* n_events; unsigned long long* n_spikes_total;
+  uint32_t* done;
+  const uint64_t* row_ptr;                    // rows of rank 0 (one rank)
+  const uint32_t* tgt; const void* w; const uint8_t* d; uint32_t w_format;
+  const float* row_scale;                     // per row (fp16 format) or null
+  uint32_t slices;
+  uint32_t deliver_grid;
+};
+
+cudaError_t launch_update(const SimArgs& a, cudaStream_t st);
+cudaError_t launch_deliver(const SimArgs& a, cudaStream_t st);
+cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st);
+
+}  // namespace snn

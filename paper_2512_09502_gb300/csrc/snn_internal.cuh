@@ -1,0 +1,173 @@
+// snn_internal.cuh -- internal declarations shared by the library's translation units.
+//
+// Record layout of the construction sort (one uint64 per synapse):
+//     record = key << cbits | cidx
+//     key    = (slot << (sb + db)) | (s << db) | d
+// slot is the source rank seen from the target rank (0 = local, then the other ranks
+// in ascending order), s the source's rank-local index, d the delay in steps and
+// cidx the synapse's global generation counter (projection counter base + projection-
+// local counter).  Sorting by the key with a stable LSD radix sort over records that
+// were written in generation order reproduces "sorted by source as first key, then
+// delay, ties in generation order" (paper, Methods, "GPU memory levels": one source's
+// connections are (first index, count)), and cidx lets the last stage regenerate the
+// target and weight of every synapse from the counter-based generator.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace snn {
+
+constexpr uint32_t kPurposeSynapse = 0;
+constexpr uint32_t kPurposeFtTarget = 1;
+constexpr uint32_t kPurposePbTest = 2;
+constexpr uint32_t kPurposePoisson = 3;
+constexpr uint32_t kPurposeVinit = 4;
+
+constexpr uint32_t kRuleFixedIndegree = 0;
+constexpr uint32_t kRuleFixedTotal = 1;
+constexpr uint32_t kRulePairwiseBernoulli = 2;
+
+// device error word bits
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrBounds = 2u;
+
+// Philox-4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 bijection with the
+// published multipliers and Weyl key increments.
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__host__ __device__ __forceinline__ uint4 philox_stream(uint64_t counter, uint32_t word2,
+                                                        uint32_t purpose, uint64_t seed) {
+  return philox4x32_10(make_uint4((uint32_t)counter, (uint32_t)(counter >> 32), word2, purpose),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// integer in [0, n): high word of w * n
+__device__ __forceinline__ uint32_t uniform_index(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+
+// uniform in (0, 1): ((w >> 9) + 0.5) * 2^-23, exact in fp32
+__device__ __forceinline__ float u01(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// floor(n / d) for 64-bit n with m = floor(2^64 / d) (2^64 - 1 for d = 1)
+__host__ __device__ __forceinline__ uint64_t div_magic(uint64_t n, uint64_t d, uint64_t m) {
+#ifdef __CUDA_ARCH__
+  uint64_t q = __umul64hi(n, m);
+#else
+  uint64_t q = (uint64_t)(((unsigned __int128)n * m) >> 64);
+#endif
+  if (n - q * d >= d) ++q;
+  return q;
+}
+
+inline uint64_t magic_for(uint64_t d) {
+  return d <= 1 ? ~0ull : (uint64_t)(((unsigned __int128)1 << 64) / d);
+}
+
+struct DevProj {
+  uint32_t src_first, n_src, src_stride;
+  uint32_t tgt_first, n_tgt, tgt_stride;
+  uint32_t rule, proj_id;
+  uint64_t K, N;            // fixed in-degree K / fixed total N
+  uint64_t pb_thr;          // Bernoulli threshold (<= 2^32)
+  uint64_t cbase, csize;    // global counter base and size
+  uint64_t seed;
+  uint64_t magic_div;       // floor(2^64 / K) (FI) or floor(2^64 / n_src) (PB)
+  uint32_t w_kind;          // 0 const, 1 normal_sign
+  float w_mean, w_sd;
+  uint32_t d_kind;          // 0 const, 1 table
+  uint32_t d_const;         // constant steps, or s_min of the table
+  uint32_t d_tbl_off, d_tbl_len;
+};
+
+// one generation block: the records of projection `proj` whose targets live on `rank`
+struct DevBlock {
+  uint64_t out_base;   // absolute position of the block's first record
+  uint64_t count;      // records in the block
+  uint64_t tile_first; // first generation tile
+  uint32_t rank, proj;
+  uint32_t ti0, tstep; // targets i = ti0 + m * tstep (projection-local index)
+  uint32_t n_t, pad;
+};
+
+struct Geom {
+  uint32_t R, rb, sb, db, key_bits, cbits;
+  uint32_t N;               // neurons
+  uint32_t pad;
+  uint64_t magic_R;         // floor(2^64 / R)
+};
+
+struct DevPop {
+  float P22, P20, P11ex, P11in, P21ex, P21in, Ie, Vth, Vreset;
+  uint32_t ref_steps;
+};
+
+struct DevDrive {
+  uint32_t first, n;
+  float weight;
+  uint32_t idx;
+  uint64_t seed;
+  uint32_t tbl_off, tbl_len;
+};
+
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t n, uint32_t v) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* a, uint32_t n, uint64_t v) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---- launchers (build.cu) ----
+struct BuildArgs {
+  const DevBlock* blocks; uint32_t nblocks; uint64_t n_gen_tiles;
+  const DevProj* projs; uint32_t nproj;
+  const uint32_t* dtables;
+  Geom g;
+  uint64_t* rec_a; uint64_t* rec_b;
+  uint64_t* hist;           // [R][passes][bins]
+  uint64_t* bin_base;       // [R][passes][bins]
+  const uint64_t* seg_start;  // [R+1]
+  const uint64_t* seg_tile0;  // [R+1] sort tiles
+  uint64_t* status;
+  uint32_t* counters;       // [passes] tile counters
+  uint32_t* err;
+  uint32_t passes, radix_bits;
+  uint64_t n_sort_tiles;
+  const uint64_t* cbase_sorted;   // [nproj] cbase of projections in id order
+  uint32_t* tgt; void* w; uint8_t* d; uint32_t w_format;
+  uint64_t* dense;          // [R][N+1] row starts (absolute)
+  const uint32_t* dense_off;  // [R][R]
+  const float* row_scale_src; // per source gid (fp16 format) or null
+  int num_sms;
+};
+
+cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
+                             uint32_t epoch, cudaStream_t st);
+cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E, cudaStream_t st);
+uint32_t sort_tile_items(uint32_t radix_bits);
+
+}  // namespace snn

@@ -82,6 +82,8 @@ class Projection:
     weight: Dist
     delay: Dist
     seed: int
+    src_stride: int = 1     # source gids src_first + i * src_stride, i < n_src
+    tgt_stride: int = 1     # target gids tgt_first + i * tgt_stride, i < n_tgt
 
 
 @dataclass(frozen=True)
