@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_
         uint64_t s = ld_status(sp);
         uint32_t spins = 0;
         while (((s >> 62) == 0) || (((s >> 46) & 0xFFFF) != (epoch & 0xFFFF))) {
-          if (++spins > SPIN_LIMIT) {
+          // bounded wait; give up at once when another wait has already timed out
+          if (++spins > SPIN_LIMIT || (*(volatile uint32_t*)a.err & kErrTimeout)) {
             atomicOr(a.err, kErrTimeout);
             s = ST_INC | ep;
             break;
