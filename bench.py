@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of on-device network construction + spike delivery on one GB300.
+
+One step = one pass of the whole hot path over one synthetic network: construction
+(counter-based generation of every synapse, the source/delay radix sort, the CSR
+layout -- ``snn_calibrate``) followed by ``--sim-steps`` simulation steps (neuron
+update + ring-buffer delivery -- ``snn_simulate``), all through the C ABI.
+
+Workload (default): the scaled balanced network, 400k E + 100k I iaf_psc_exp neurons,
+fixed in-degree 9,000 E + 2,250 I (5.625G synapses, 50.6 GB layout), delays
+normal(1.5, 0.75) ms clipped at 0.1 ms, Poisson drive tuned so that the network fires
+at about 8 Hz, 10,000 steps of 0.1 ms.  The metric counts synapses built plus synaptic
+events delivered per second of the step.
+
+``--impl reference`` times the CPU oracle (``oracle/``) on a bounded sample of the
+same workload instead.  Under torchrun each rank builds and simulates its own replica
+(weak scaling; the path needs no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "synapses built/s + synaptic events/s (1 GB300, % HBM peak), bf16 vs fp32 weights"
+UNIT = "(synapses + events)/s"
+# algorithmic bytes per unit of the measured kernels
+BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize": 17.0, "generate": 8.0}
+
+
+def workload(name: str, scale: float):
+    from paper_2512_09502_gb300 import workloads as wl
+    if name == "balanced_500k":
+        return wl.balanced_scaled(scale)
+    if name == "balanced_5k":
+        return wl.balanced_small()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def traffic_of(kernel: str, units_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2512_09502_gb300", "csrc", d["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+        return None
+    return d["dram_bytes_per_unit"] * units_per_launch
+
+
+def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000):
+    """The oracle on a bounded sample of the workload: the same balanced network
+    (same in-degrees, weights, delays, drive, hence the same dynamical regime) at
+    ``n_neurons`` neurons, built and then simulated for ``sim_steps`` steps."""
+    import numpy as np
+    from oracle import connect as oc, layout as ol, neuron as on
+    from paper_2512_09502_gb300 import workloads as wl
+    net = wl.balanced_scaled(scale * n_neurons / 500_000)
+    t0 = time.perf_counter()
+    syn = oc.generate(net)
+    rk = ol.build_rank(syn, ol.round_robin(net.n_neurons, 1), 0)
+    sim = on.Simulator(net, rk["row_ptr"], rk["tgt"], rk["d"], rk["w"].astype(np.float32).astype(np.float64),
+                       on.ring_slots_for(oc.max_delay(net)))
+    spikes, _ = sim.run(sim_steps)
+    g = np.array([x for _, x in spikes], dtype=np.int64)
+    events = int(np.sum(rk["row_ptr"][g + 1] - rk["row_ptr"][g])) if len(g) else 0
+    dt = time.perf_counter() - t0
+    units = len(syn["src"]) + events
+    return units / dt, dict(synapses=len(syn["src"]), events=events, seconds=dt,
+                            sample=f"balanced network with the workload's in-degrees, weights, delays and "
+                                   f"drive at {net.n_neurons} neurons ({len(syn['src'])} synapses), built "
+                                   f"then simulated {sim_steps} steps ({events} events)")
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
+    vals, info = [], None
+    t0 = time.perf_counter()
+    units = 0.0
+    for _ in range(args.steps):
+        v, info = cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
+        units += info["synapses"] + info["events"]
+        vals.append(v)
+    dt = time.perf_counter() - t0
+    value = units / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": info["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2512_09502_gb300 import _lib, build
+    build.build()
+    net = workload(args.workload, args.scale)
+    alloc = _lib.TorchAllocator(local)
+    stream = torch.cuda.current_stream()
+
+    def one(fmt, sim_steps, profile=False):
+        ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
+                                 device=local, use_graph=True, profile_kernels=profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.calibrate()
+        ctx.simulate(sim_steps)
+        e1.record(stream)
+        e1.synchronize()
+        st = ctx.stats()
+        ctx.destroy()
+        return e0.elapsed_time(e1), st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def timed(fmt):
+        for _ in range(args.warmup):
+            one(fmt, args.sim_steps)
+        barrier()
+        clk = Clocks(local)
+        clk.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        stats = []
+        for _ in range(args.steps):
+            stats.append(one(fmt, args.sim_steps)[1])
+        t1.record(stream)
+        barrier()
+        clocks = clk.stop()
+        ms = max_over_ranks(t0.elapsed_time(t1))
+        units = sum(s["n_synapses"] + s["n_events"] for s in stats)
+        return ms, sum_over_ranks(units), stats, clocks
+
+    ms, units, stats, clocks = timed("f32")
+    value = units / (ms / 1000.0)
+    s0 = stats[-1]
+    syn_per_s = s0["n_synapses"] / (s0["t_calibrate_ms"] / 1000.0)
+    ev_per_s = s0["n_events"] / (s0["t_simulate_ms"] / 1000.0) if s0["t_simulate_ms"] else 0.0
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # BF16-weight form of the same workload
+    bf = None
+    if not args.no_bf16:
+        ms_b, units_b, stats_b, _ = timed("bf16")
+        sb = stats_b[-1]
+        bf = {"value": units_b / (ms_b / 1000.0),
+              "synapses_built_per_s": sb["n_synapses"] / (sb["t_calibrate_ms"] / 1000.0),
+              "synaptic_events_per_s": sb["n_events"] / (sb["t_simulate_ms"] / 1000.0) if sb["t_simulate_ms"] else 0.0}
+        bf["events_per_s_vs_f32"] = bf["synaptic_events_per_s"] / ev_per_s if ev_per_s else None
+
+    # end to end through the public API: host spec in, stats (the result) out
+    e2e_ms, e2e_units, h2d, d2h = 0.0, 0.0, 0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx = _lib.build_network(net, weight_format="f32", allocator=alloc, stream=stream.cuda_stream,
+                                 device=local, use_graph=True)
+        ctx.calibrate()
+        ctx.simulate(args.sim_steps)
+        st = ctx.stats()
+        ctx.destroy()
+        e2e_ms += 1000 * (time.perf_counter() - t)
+        e2e_units += st["n_synapses"] + st["n_events"]
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_units = sum_over_ranks(e2e_units)
+
+    # per-kernel CUDA-event times for the roofline (outside the timed region)
+    _, prof = one("f32", min(args.sim_steps, 2000), profile=True)
+    peak, peak_kind = peaks()
+    E = prof["n_synapses"]
+    per_pass_ms = prof["t_sort_pass_ms"] / max(prof["sort_passes"], 1)
+    deliver_ms = prof["t_deliver_ms"] / max(prof["deliver_launches"], 1)
+    events_per_launch = prof["n_events"] / max(prof["deliver_launches"], 1)
+    step_ms = ms / args.steps
+    share = {"sort_pass": prof["t_sort_pass_ms"] / step_ms,
+             "deliver": deliver_ms * args.sim_steps / step_ms}
+    dominant = max(share, key=share.get)
+    if dominant == "sort_pass":
+        alg = E * BYTES["sort_pass"]
+        ach = alg / (per_pass_ms / 1000.0) / 1e9
+        kern, units_launch = "onesweep_pass", E
+    else:
+        alg = events_per_launch * BYTES["deliver_f32"]
+        ach = alg / (deliver_ms / 1000.0) / 1e9
+        kern, units_launch = "deliver_kernel", events_per_launch
+    roof = {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic_of(kern, units_launch),
+            "algorithmic_bytes_per_launch": alg,
+            "shares_of_step": share,
+            "sort_pass": {"ms_per_launch": per_pass_ms, "GBps": E * 16 / (per_pass_ms / 1000) / 1e9},
+            "deliver": {"ms_per_launch": deliver_ms, "events_per_launch": events_per_launch,
+                        "GBps": events_per_launch * 13 / (deliver_ms / 1000) / 1e9 if deliver_ms else None},
+            "update": {"ms_per_launch": prof["t_update_ms"] / max(prof["update_launches"], 1)}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, info = cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "neurons": net.n_neurons, "synapses": s0["n_synapses"],
+                       "sim_steps": args.sim_steps, "dt_ms": net.dt, "drive_hz": net.drives[0].rate_hz if net.drives else 0.0,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "working set (50.6 GB layout) far larger than L2"},
+            "components": {"synapses_built_per_s": syn_per_s, "synaptic_events_per_s": ev_per_s,
+                           "construct_ms": s0["t_calibrate_ms"], "simulate_ms": s0["t_simulate_ms"],
+                           "generate_ms": s0["t_generate_ms"], "sort_ms": s0["t_sort_ms"],
+                           "finalize_ms": s0["t_finalize_ms"], "events_per_step": s0["n_events"] / args.sim_steps,
+                           "rate_hz": s0["n_spikes"] / net.n_neurons / (args.sim_steps * net.dt / 1000.0),
+                           "peak_device_GB": s0["peak_device_bytes"] / 1e9},
+            "bf16": bf,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="balanced_500k")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--sim-steps", type=int, default=10_000)
+    ap.add_argument("--ref-neurons", type=int, default=1000)
+    ap.add_argument("--ref-sim-steps", type=int, default=1000)
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

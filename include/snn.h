@@ -97,6 +97,8 @@ typedef struct snn_config {
   uint64_t spike_log_capacity; /* spikes kept for snn_get_spikes; 0 = no recording    */
   int32_t radix_bits;          /* sort digit width 8..11; 0 = tuned default            */
   int32_t device;              /* CUDA device ordinal                                  */
+  int32_t profile_kernels;     /* time every update / deliver launch with CUDA events
+                                  (no graph then); results in snn_stats_t              */
 } snn_config;
 
 /* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in
@@ -127,6 +129,12 @@ typedef struct snn_stats_t {
   double t_simulate_ms;
   uint32_t sort_passes, radix_bits, key_bits, ring_slots;
   uint32_t gen_kernel_launches, sort_kernel_launches;
+  uint64_t kernel_launches;                  /* library kernels launched so far   */
+  uint64_t h2d_bytes, d2h_bytes;             /* host<->device bytes copied so far */
+  /* per-kernel CUDA-event times (sort passes always; update / deliver only with
+     profile_kernels) and their launch counts */
+  double t_sort_pass_ms, t_update_ms, t_deliver_ms;
+  uint64_t update_launches, deliver_launches;
 } snn_stats_t;
 
 /* ---- lifecycle -----------------------------------------------------------

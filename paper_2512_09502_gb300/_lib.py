@@ -43,7 +43,8 @@ class snn_allocator(C.Structure):
 class snn_config(C.Structure):
     _fields_ = [("dt_ms", C.c_double), ("n_ranks", C.c_uint32), ("weight_format", C.c_int32),
                 ("exchange", C.c_int32), ("use_graph", C.c_int32),
-                ("spike_log_capacity", C.c_uint64), ("radix_bits", C.c_int32), ("device", C.c_int32)]
+                ("spike_log_capacity", C.c_uint64), ("radix_bits", C.c_int32), ("device", C.c_int32),
+                ("profile_kernels", C.c_int32)]
 
 
 class snn_iaf_psc_exp_params(C.Structure):
@@ -67,7 +68,10 @@ class snn_stats_t(C.Structure):
                [(n, C.c_double) for n in ["t_generate_ms", "t_sort_ms", "t_finalize_ms", "t_maps_ms",
                                           "t_calibrate_ms", "t_simulate_ms"]] + \
                [(n, C.c_uint32) for n in ["sort_passes", "radix_bits", "key_bits", "ring_slots",
-                                          "gen_kernel_launches", "sort_kernel_launches"]]
+                                          "gen_kernel_launches", "sort_kernel_launches"]] + \
+               [(n, C.c_uint64) for n in ["kernel_launches", "h2d_bytes", "d2h_bytes"]] + \
+               [(n, C.c_double) for n in ["t_sort_pass_ms", "t_update_ms", "t_deliver_ms"]] + \
+               [(n, C.c_uint64) for n in ["update_launches", "deliver_launches"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -153,10 +157,11 @@ class Context:
     def __init__(self, *, dt: float = 0.1, n_ranks: int = 1, weight_format: str = "f32",
                  exchange: str = "p2p", use_graph: bool = True, spike_log_capacity: int = 0,
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, profile_kernels: bool = False):
         self.lib = load()
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
-                         1 if use_graph else 0, spike_log_capacity, radix_bits, device)
+                         1 if use_graph else 0, spike_log_capacity, radix_bits, device,
+                         1 if profile_kernels else 0)
         self._allocator = allocator
         h = C.c_void_p()
         rc = self.lib.snn_create(C.byref(cfg), C.byref(allocator.struct) if allocator else None,

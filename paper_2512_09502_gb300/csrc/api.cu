@@ -93,6 +93,7 @@ struct snn_ctx {
   uint32_t ring_slots = 0;
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_steps = 0;
+  bool capturing = false;
   std::vector<uint32_t> host_gid_of;      // position -> gid
   std::vector<uint32_t> host_pos_of;      // gid -> position
 };
@@ -156,6 +157,7 @@ template <typename T>
 int upload(snn_ctx* c, T** out, const std::vector<T>& v, const char* what) {
   AL(*out, std::max<size_t>(v.size(), 1), what);
   if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
+  c->stats.h2d_bytes += v.size() * sizeof(T);
   return SNN_OK;
 }
 
@@ -538,12 +540,18 @@ int snn_calibrate(snn_ctx* c) {
   a.dense_off = c->d_dense_off;
 
   CK(launch_generate(a, c->st));
+  c->stats.kernel_launches += tiles ? 1 : 0;
   CK(cudaEventRecord(ev[1], c->st));
   CK(launch_bin_scan(a, c->st));
+  c->stats.kernel_launches += passes ? 1 : 0;
+  cudaEvent_t evp;
+  CK(cudaEventCreate(&evp));
+  CK(cudaEventRecord(evp, c->st));
   uint64_t* cur = rec_a;
   uint64_t* oth = rec_b;
   for (uint32_t p = 0; p < passes; ++p) {
     CK(launch_sort_pass(a, p, cur, oth, p + 1, c->st));
+    c->stats.kernel_launches += n_sort_tiles ? 1 : 0;
     std::swap(cur, oth);
   }
   CK(cudaEventRecord(ev[2], c->st));
@@ -578,6 +586,7 @@ int snn_calibrate(snn_ctx* c) {
   a.tgt = c->d_tgt; a.w = c->d_w; a.d = c->d_d; a.w_format = (uint32_t)c->cfg.weight_format;
   a.dense = c->d_dense; a.row_scale_src = c->d_scale_src;
   CK(launch_finalize(a, cur, E, c->st));
+  c->stats.kernel_launches += E ? 2 : 1;
   CK(cudaEventRecord(ev[3], c->st));
   dfree(c, cur);
   dfree(c, d_blocks);
@@ -671,14 +680,19 @@ int snn_calibrate(snn_ctx* c) {
     if (rc != SNN_OK) return rc;
   }
   CK(launch_init_state(s, d_v0, c->st));
+  c->stats.kernel_launches += 1;
   CK(cudaEventRecord(ev[5], c->st));
   CK(cudaStreamSynchronize(c->st));
   dfree(c, d_v0);
   uint32_t herr = 0;
   CK(cudaMemcpy(&herr, c->d_err, 4, cudaMemcpyDeviceToHost));
-  float ms[5];
+  c->stats.d2h_bytes += 4;
+  float ms[5], ms_pass = 0;
   for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]));
+  CK(cudaEventElapsedTime(&ms_pass, evp, ev[2]));
   for (auto& e : ev) cudaEventDestroy(e);
+  cudaEventDestroy(evp);
+  c->stats.t_sort_pass_ms = ms_pass;
   c->stats.t_generate_ms = ms[0];
   c->stats.t_sort_ms = ms[1];
   c->stats.t_finalize_ms = ms[2];
@@ -706,12 +720,38 @@ static int run_steps(snn_ctx* c, uint32_t steps) {
       CK(launch_route(c));
       CK(launch_deliver(s, c->st));
     }
+    if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * (2 + route_kernels_per_step(c));
+    return SNN_OK;
+  }
+  if (c->cfg.profile_kernels && !c->capturing) {
+    std::vector<cudaEvent_t> evs(3 * (size_t)steps);
+    for (auto& e : evs) CK(cudaEventCreate(&e));
+    for (uint32_t k = 0; k < steps; ++k) {
+      CK(cudaEventRecord(evs[3 * k], c->st));
+      CK(launch_update(s, c->st));
+      CK(cudaEventRecord(evs[3 * k + 1], c->st));
+      CK(launch_deliver(s, c->st));
+      CK(cudaEventRecord(evs[3 * k + 2], c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    for (uint32_t k = 0; k < steps; ++k) {
+      float u = 0, d = 0;
+      CK(cudaEventElapsedTime(&u, evs[3 * k], evs[3 * k + 1]));
+      CK(cudaEventElapsedTime(&d, evs[3 * k + 1], evs[3 * k + 2]));
+      c->stats.t_update_ms += u;
+      c->stats.t_deliver_ms += d;
+    }
+    for (auto& e : evs) cudaEventDestroy(e);
+    c->stats.update_launches += steps;
+    c->stats.deliver_launches += steps;
+    c->stats.kernel_launches += (uint64_t)steps * 2;
     return SNN_OK;
   }
   for (uint32_t k = 0; k < steps; ++k) {
     CK(launch_update(s, c->st));
     CK(launch_deliver(s, c->st));
   }
+  if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * 2;
   return SNN_OK;
 }
 
@@ -721,7 +761,9 @@ static int build_graph(snn_ctx* c, uint32_t steps) {
   cudaStream_t keep = c->st;
   c->st = cap;
   CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
   int rc = run_steps(c, steps);
+  c->capturing = false;
   cudaGraph_t gr;
   cudaError_t e = cudaStreamEndCapture(cap, &gr);
   c->st = keep;
@@ -743,7 +785,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, c->st));
   uint32_t left = steps;
-  if (c->cfg.use_graph) {
+  if (c->cfg.use_graph && !c->cfg.profile_kernels) {
     const uint32_t G = 10;
     if (!c->graph && steps >= G) {
       int rc = build_graph(c, G);
@@ -752,6 +794,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
     while (c->graph && left >= c->graph_steps) {
       CK(cudaGraphLaunch(c->graph, c->st));
       left -= c->graph_steps;
+      c->stats.kernel_launches += (uint64_t)c->graph_steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0));
     }
   }
   int rc = run_steps(c, left);
@@ -766,6 +809,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
   c->stats.steps_done += steps;
   uint32_t herr = 0;
   CK(cudaMemcpy(&herr, c->d_err, 4, cudaMemcpyDeviceToHost));
+  c->stats.d2h_bytes += 4;
   if (herr & kErrTimeout) return fail(c, SNN_ETIMEOUT, "a bounded device wait gave up during simulation");
   if (herr) return fail(c, SNN_ECUDA, "device-side bounds check failed during simulation");
   return SNN_OK;
@@ -922,6 +966,7 @@ int snn_stats(snn_ctx* c, snn_stats_t* out) {
     unsigned long long v[2] = {0, 0};
     CK(cudaMemcpy(&v[0], c->sim.n_spikes_total, 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&v[1], c->sim.n_events, 8, cudaMemcpyDeviceToHost));
+    c->stats.d2h_bytes += 16;
     s.n_spikes = v[0];
     s.n_events = v[1];
   }

@@ -16,6 +16,8 @@ int setup_routing(snn_ctx* c) { return ctx_fail(c, SNN_EINVAL, "logical ranks > 
 
 cudaError_t launch_route(snn_ctx*) { return cudaErrorNotSupported; }
 
+uint32_t route_kernels_per_step(snn_ctx*) { return 0; }
+
 int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp) {
   const Geom& g = ctx_geom(c);
   if (g.R != 1) return ctx_fail(c, SNN_EINVAL, "logical ranks > 1 are not built yet");

@@ -41,6 +41,7 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
                const uint64_t* d_cbase);
 int setup_routing(snn_ctx* c);
 cudaError_t launch_route(snn_ctx* c);
+uint32_t route_kernels_per_step(snn_ctx* c);
 int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp);
 int rank_row_scales(snn_ctx* c, uint32_t rank, std::vector<float>* scales);
 int rank_row_bounds(snn_ctx* c, uint32_t rank, uint64_t row, uint64_t ab[2], float* scale);
