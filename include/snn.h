@@ -201,7 +201,9 @@ int snn_get_spikes(snn_ctx* ctx, uint32_t* host_step, uint32_t* host_gid, uint64
                    uint64_t* n_out);
 
 /* Copy V (mV), I_ex, I_in (pA) of gids [first, first + n) into host arrays (any may be
- * NULL). */
+ * NULL).  When every population has tau_syn_ex == tau_syn_in the two receptors share
+ * one ring buffer and one current: I_ex then holds the total synaptic current and I_in
+ * is 0 (the membrane dynamics are identical). */
 int snn_get_state(snn_ctx* ctx, uint32_t first, uint32_t n, float* host_V, float* host_Iex,
                   float* host_Iin);
 

@@ -21,6 +21,11 @@ Spike delivery (Appendix, point-to-point example, delivery figure): a spike of s
 through a connection of delay d (>= 1 step) and weight w adds w to slot (n + d) mod D
 of the target's ring for receptor ex (w >= 0) or in (w < 0).
 
+Reading: the method computes the propagators in FP64 and stores them in FP32; the
+simulator can take them that way (``stored_fp32``), which is what network-level
+comparisons use -- the balanced networks are chaotic, so a 3e-8 relative change of a
+constant alone moves 1-s population rates by several percent.
+
 Pinned by tests/test_oracle_neuron.py: the closed-form PSP at grid points, the
 steady state and the closed-form inter-spike interval under constant current, the
 tau_syn -> tau_m limit, and the delivery slots of the worked example.
@@ -78,7 +83,10 @@ def initial_v(net):
 class Simulator:
     """Plain per-step simulation over a global source-sorted layout (rows = gids)."""
 
-    def __init__(self, net, row_ptr, tgt, d, w, ring_slots: int):
+    def __init__(self, net, row_ptr, tgt, d, w, ring_slots: int, stored_fp32: bool = False):
+        """``stored_fp32``: use the propagators as the method stores them -- computed
+        in FP64, rounded once to FP32 (like the stored weights).  The membrane and
+        current arithmetic stays FP64 either way."""
         self.net = net
         self.N = net.n_neurons
         self.h = net.dt
@@ -89,7 +97,8 @@ class Simulator:
         for pop in net.populations:
             pr = propagators(pop.params, self.h)
             for f in fields:
-                per[f].append(np.full(pop.n, pr[f]))
+                v = float(np.float32(pr[f])) if stored_fp32 else pr[f]
+                per[f].append(np.full(pop.n, v))
             per["ref_steps"].append(np.full(pop.n, pr["ref_steps"], dtype=np.int64))
             per["I_e"].append(np.full(pop.n, pop.params.I_e))
             per["V_th"].append(np.full(pop.n, pop.params.V_th))

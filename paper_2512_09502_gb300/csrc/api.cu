@@ -417,10 +417,6 @@ int snn_calibrate(snn_ctx* c) {
   for (uint32_t i = 0; i < P; ++i) {
     const ProjSpec& s = c->projs[i];
     DevProj& d = dp[i];
-    if (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI)
-      return fail(c, SNN_EINVAL, "pairwise Bernoulli is not built on the GPU path yet");
-    if (s.rule.kind == SNN_RULE_FIXED_TOTAL && R > 1)
-      return fail(c, SNN_EINVAL, "fixed total number over several ranks is not built yet");
     d.src_first = s.src_first; d.n_src = s.n_src; d.src_stride = s.src_stride;
     d.tgt_first = s.tgt_first; d.n_tgt = s.n_tgt; d.tgt_stride = s.tgt_stride;
     d.rule = (uint32_t)s.rule.kind; d.proj_id = i; d.seed = s.seed;
@@ -455,15 +451,77 @@ int snn_calibrate(snn_ctx* c) {
   const uint32_t passes = (g.key_bits + RB - 1) / RB;
   if (passes > 6) return fail(c, SNN_EINVAL, "sort key too wide");
 
+  // ---- counted projections: fixed total over several ranks, pairwise Bernoulli ----
+  DevProj* d_projs;
+  UP(d_projs, dp, "projections");
+  std::vector<uint32_t> ft_proj, pb_proj;
+  std::vector<uint64_t> ft_tile_first(1, 0), pb_t_first(1, 0);
+  for (uint32_t i = 0; i < P; ++i) {
+    const ProjSpec& s = c->projs[i];
+    if (s.rule.kind == SNN_RULE_FIXED_TOTAL && R > 1) {
+      ft_proj.push_back(i);
+      ft_tile_first.push_back(ft_tile_first.back() + ((uint64_t)s.rule.param + kCountTile - 1) / kCountTile);
+    } else if (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI) {
+      pb_proj.push_back(i);
+      pb_t_first.push_back(pb_t_first.back() + s.n_tgt);
+    }
+  }
+  const bool counted = !ft_proj.empty() || !pb_proj.empty();
+  CountedArgs ca{};
+  std::vector<uint64_t> ft_tot_h, pb_tot_h;
+  std::vector<void*> counted_bufs;
+  if (counted) {
+    if (R > kMaxCountedRanks) return fail(c, SNN_EINVAL, "fixed total / Bernoulli support at most 1024 ranks");
+    uint32_t *d_ftp, *d_pbp;
+    uint64_t *d_ftf, *d_pbf;
+    UP(d_ftp, ft_proj, "fixed-total list");
+    UP(d_pbp, pb_proj, "Bernoulli list");
+    UP(d_ftf, ft_tile_first, "fixed-total tiles");
+    UP(d_pbf, pb_t_first, "Bernoulli targets");
+    ca.projs = d_projs; ca.R = R; ca.magic_R = magic_for(R);
+    ca.ft_proj = d_ftp; ca.ft_tile_first = d_ftf; ca.n_ft = (uint32_t)ft_proj.size();
+    ca.n_ft_tiles = ft_tile_first.back();
+    ca.pb_proj = d_pbp; ca.pb_t_first = d_pbf; ca.n_pb = (uint32_t)pb_proj.size();
+    ca.n_pb_targets = pb_t_first.back();
+    AL(ca.ft_tile_cnt, std::max<uint64_t>(ca.n_ft_tiles * R, 1), "fixed-total tile counts");
+    AL(ca.ft_tile_off, std::max<uint64_t>(ca.n_ft_tiles * R, 1), "fixed-total tile offsets");
+    AL(ca.ft_tot, std::max<uint64_t>((uint64_t)ca.n_ft * R, 1), "fixed-total block sizes");
+    AL(ca.pb_cnt, std::max<uint64_t>(ca.n_pb_targets, 1), "Bernoulli counts");
+    AL(ca.pb_off, std::max<uint64_t>(ca.n_pb_targets, 1), "Bernoulli offsets");
+    AL(ca.pb_tot, std::max<uint64_t>((uint64_t)ca.n_pb * R, 1), "Bernoulli block sizes");
+    counted_bufs = {d_ftp, d_pbp, d_ftf, d_pbf, ca.ft_tile_cnt, ca.ft_tile_off, ca.ft_tot, ca.pb_cnt, ca.pb_off,
+                    ca.pb_tot};
+    CK(launch_counted_count(ca, c->st, c->num_sms));
+    c->stats.kernel_launches += (ca.n_ft_tiles ? 2 : 0) + (ca.n_pb_targets ? 2 : 0);
+    ft_tot_h.resize((size_t)ca.n_ft * R);
+    pb_tot_h.resize((size_t)ca.n_pb * R);
+    if (!ft_tot_h.empty())
+      CK(cudaMemcpyAsync(ft_tot_h.data(), ca.ft_tot, ft_tot_h.size() * 8, cudaMemcpyDeviceToHost, c->st));
+    if (!pb_tot_h.empty())
+      CK(cudaMemcpyAsync(pb_tot_h.data(), ca.pb_tot, pb_tot_h.size() * 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->stats.d2h_bytes += (ft_tot_h.size() + pb_tot_h.size()) * 8;
+  }
+
   // ---- generation blocks: rank-major, then projection order ----
   std::vector<DevBlock> blocks;
+  std::vector<uint64_t> block_base(counted ? (size_t)P * R : 0, 0);
   c->seg_start.assign(R + 1, 0);
   const uint64_t GEN_TILE = 4096;
   uint64_t pos = 0, tiles = 0;
   for (uint32_t t = 0; t < R; ++t) {
     c->seg_start[t] = pos;
+    uint32_t kft = 0, kpb = 0;
     for (uint32_t i = 0; i < P; ++i) {
       const ProjSpec& s = c->projs[i];
+      const bool is_ft_counted = s.rule.kind == SNN_RULE_FIXED_TOTAL && R > 1;
+      const bool is_pb = s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI;
+      if (counted) block_base[(size_t)i * R + t] = pos;
+      if (is_ft_counted || is_pb) {
+        const uint32_t q = is_pb ? kpb++ : kft++;
+        pos += is_pb ? pb_tot_h[(size_t)q * R + t] : ft_tot_h[(size_t)q * R + t];
+        continue;
+      }
       DevBlock b{};
       b.rank = t; b.proj = i;
       // targets tgt_first + ti * stride living on rank t: one residue class of ti
@@ -508,9 +566,14 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- device buffers for the build ----
   BuildArgs a{};
-  DevBlock* d_blocks; DevProj* d_projs; uint32_t* d_dtab; uint64_t* d_seg_tile0; uint64_t* d_cbase;
+  DevBlock* d_blocks; uint32_t* d_dtab; uint64_t* d_seg_tile0; uint64_t* d_cbase;
   UP(d_blocks, blocks, "blocks");
-  UP(d_projs, dp, "projections");
+  if (counted) {
+    uint64_t* d_bb;
+    UP(d_bb, block_base, "block bases");
+    ca.block_base = d_bb;
+    counted_bufs.push_back(d_bb);
+  }
   UP(d_dtab, dtab, "delay tables");
   UP(c->d_seg_start, c->seg_start, "segments");
   UP(d_seg_tile0, seg_tile0, "sort tiles");
@@ -538,9 +601,15 @@ int snn_calibrate(snn_ctx* c) {
   a.counters = counters; a.err = c->d_err; a.passes = passes; a.radix_bits = RB;
   a.n_sort_tiles = n_sort_tiles; a.cbase_sorted = d_cbase; a.num_sms = c->num_sms;
   a.dense_off = c->d_dense_off;
+  a.fuse_hist = counted ? 0u : 1u;
 
   CK(launch_generate(a, c->st));
   c->stats.kernel_launches += tiles ? 1 : 0;
+  if (counted) {
+    CK(launch_counted_place(ca, a, c->st));
+    CK(launch_histogram(a, c->st));
+    c->stats.kernel_launches += (ca.n_ft_tiles ? 1 : 0) + (ca.n_pb_targets ? 1 : 0) + 1;
+  }
   CK(cudaEventRecord(ev[1], c->st));
   CK(launch_bin_scan(a, c->st));
   c->stats.kernel_launches += passes ? 1 : 0;
@@ -591,6 +660,7 @@ int snn_calibrate(snn_ctx* c) {
   dfree(c, cur);
   dfree(c, d_blocks);
   dfree(c, counters);
+  for (void* p : counted_bufs) dfree(c, p);
 
   // ---- image neurons and communication maps (logical ranks) ----
   if (R > 1) {
@@ -652,29 +722,38 @@ int snn_calibrate(snn_ctx* c) {
   UP(d_ptab, ptab, "Poisson tables");
   s.drives = d_dr; s.ndrives = (uint32_t)ddr.size();
   s.poisson_tbl = d_ptab; s.poisson_tbl_len = (uint32_t)ptab.size();
-  AL(s.ring, (uint64_t)D * 2 * N, "ring buffers");
-  CK(cudaMemsetAsync(s.ring, 0, (size_t)D * 2 * N * 4, c->st));
+  bool merged = true;
+  for (const auto& ps : c->pops) merged = merged && ps.p.tau_syn_ex == ps.p.tau_syn_in;
+  s.n_rec = merged ? 1 : 2;
+  AL(s.ring, (uint64_t)D * s.n_rec * N, "ring buffers");
+  CK(cudaMemsetAsync(s.ring, 0, (size_t)D * s.n_rec * N * 4, c->st));
   s.ring_mask = D - 1;
   AL(s.step, 1, "step");
-  AL(s.n_items, 2, "item counts");
-  AL(s.items, (uint64_t)2 * N, "items");
+  AL(s.n_spk, 2, "spike counts");
+  AL(s.spk, (uint64_t)2 * N, "spike lists");
+  s.work = s.spk; s.n_work = s.n_spk; s.work_stride = N;      // one rank: rows = neurons
   AL(s.n_logged, 1, "log count");
   AL(s.n_events, 1, "event count");
   AL(s.n_spikes_total, 1, "spike count");
   AL(s.done, 1, "done ticket");
   CK(cudaMemsetAsync(s.step, 0, 4, c->st));
-  CK(cudaMemsetAsync(s.n_items, 0, 8, c->st));
+  CK(cudaMemsetAsync(s.n_spk, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_logged, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_events, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_spikes_total, 0, 8, c->st));
   CK(cudaMemsetAsync(s.done, 0, 4, c->st));
   s.log_cap = c->cfg.spike_log_capacity;
   if (s.log_cap) AL(s.log, s.log_cap, "spike log");
-  s.row_ptr = c->d_dense;
+  s.rows = c->d_dense;
   s.tgt = c->d_tgt; s.w = c->d_w; s.d = c->d_d; s.w_format = (uint32_t)c->cfg.weight_format;
   s.row_scale = c->d_row_scale;
-  s.slices = 4;
+  // rows split into slices of about 1,024 events so that every CTA gets work
+  {
+    const double avg = E ? (double)E / std::max<uint64_t>(1, (uint64_t)N) : 0.0;
+    s.slices = (uint32_t)std::min(64.0, std::max(1.0, std::ceil(avg / 1024.0)));
+  }
   s.deliver_grid = (uint32_t)c->num_sms * 8;
+  s.update_grid = (uint32_t)c->num_sms * 8;
   if (R > 1) {
     int rc = setup_routing(c);
     if (rc != SNN_OK) return rc;
@@ -1001,6 +1080,7 @@ const std::vector<uint64_t>& ctx_seg_start(snn_ctx* c) { return c->seg_start; }
 const std::vector<uint32_t>& ctx_rank_sizes(snn_ctx* c) { return c->M; }
 const std::vector<uint32_t>& ctx_rank_off(snn_ctx* c) { return c->rank_off; }
 uint64_t* ctx_dense(snn_ctx* c) { return c->d_dense; }
+const uint32_t* ctx_dense_off(snn_ctx* c) { return c->d_dense_off; }
 const uint64_t* ctx_dseg_start(snn_ctx* c) { return c->d_seg_start; }
 const float* ctx_scale_src(snn_ctx* c) { return c->d_scale_src; }
 int ctx_num_sms(snn_ctx* c) { return c->num_sms; }

@@ -112,9 +112,11 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       if (P.d_kind == 1) d += upper_bound_u32(s_tbl, P.d_tbl_len, b.y);
       const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
       a.rec_a[blk.out_base + e] = (kk << g.cbits) | ((P.cbase + c) & cmask);
+      if (a.fuse_hist) {
 #pragma unroll
-      for (int p = 0; p < MAX_PASSES; ++p)
-        if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+        for (int p = 0; p < MAX_PASSES; ++p)
+          if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+      }
     }
   }
   __syncthreads();
@@ -335,6 +337,268 @@ cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* 
   if (a.n_sort_tiles == 0) return cudaSuccess;
   if (a.radix_bits != 8) return cudaErrorInvalidValue;
   onesweep_pass<8><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, 0, st>>>(a, pass, in, out, epoch);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// counted generation: fixed total over several ranks, pairwise Bernoulli
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rank_of(uint32_t g, uint32_t R, uint64_t magic_R) {
+  return g - (uint32_t)div_magic(g, R, magic_R) * R;
+}
+
+// record of one synapse (source from w0, delay from w1) on target rank `rank`
+__device__ __forceinline__ uint64_t make_record(const DevProj& P, const Geom& g, uint32_t rank, uint64_t c,
+                                                uint32_t src, uint32_t w1, const uint32_t* tbl) {
+  uint32_t sig = 0, s = src;
+  if (g.R > 1) {
+    s = (uint32_t)div_magic(src, g.R, g.magic_R);
+    sig = src - s * g.R;
+  }
+  const uint32_t slot = sig == rank ? 0u : (sig < rank ? sig + 1 : sig);
+  uint32_t d = P.d_const;
+  if (P.d_kind == 1) d += upper_bound_u32(tbl, P.d_tbl_len, w1);
+  const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
+  const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
+  return (kk << g.cbits) | ((P.cbase + c) & cmask);
+}
+
+__device__ __forceinline__ uint32_t pb_word(const DevProj& P, uint64_t q) {
+  const uint4 tb = philox_stream(q >> 2, P.proj_id, kPurposePbTest, P.seed);
+  const uint32_t lane = (uint32_t)(q & 3);
+  return lane == 0 ? tb.x : lane == 1 ? tb.y : lane == 2 ? tb.z : tb.w;
+}
+
+__global__ void __launch_bounds__(256) ft_count_kernel(CountedArgs c) {
+  __shared__ uint32_t s_cnt[kMaxCountedRanks];
+  for (uint64_t tile = blockIdx.x; tile < c.n_ft_tiles; tile += gridDim.x) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < c.R; i += blockDim.x) s_cnt[i] = 0;
+    const uint32_t q = upper_bound_u64(c.ft_tile_first, c.n_ft, tile) - 1;
+    const DevProj& P = c.projs[c.ft_proj[q]];
+    __syncthreads();
+    const uint64_t j0 = (tile - c.ft_tile_first[q]) * kCountTile;
+    const uint32_t n = (uint32_t)min((uint64_t)kCountTile, P.N - j0);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint4 bt = philox_stream(j0 + i, P.proj_id, kPurposeFtTarget, P.seed);
+      const uint32_t t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
+      atomicAdd(&s_cnt[rank_of(t, c.R, c.magic_R)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < c.R; i += blockDim.x) c.ft_tile_cnt[tile * c.R + i] = s_cnt[i];
+  }
+}
+
+// one thread per (projection, rank): running offsets over the projection's tiles
+__global__ void ft_scan_kernel(CountedArgs c) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (uint64_t)c.n_ft * c.R) return;
+  const uint32_t q = (uint32_t)(k / c.R), r = (uint32_t)(k - (uint64_t)q * c.R);
+  uint64_t acc = 0;
+  for (uint64_t t = c.ft_tile_first[q]; t < c.ft_tile_first[q + 1]; ++t) {
+    c.ft_tile_off[t * c.R + r] = acc;
+    acc += c.ft_tile_cnt[t * c.R + r];
+  }
+  c.ft_tot[k] = acc;
+}
+
+// one warp per target of a Bernoulli projection: pairs kept
+__global__ void pb_count_kernel(CountedArgs c) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < c.n_pb_targets; x += nwarps) {
+    const uint32_t q = upper_bound_u64(c.pb_t_first, c.n_pb, x) - 1;
+    const DevProj& P = c.projs[c.pb_proj[q]];
+    const uint64_t ti = x - c.pb_t_first[q];
+    uint32_t cnt = 0;
+    for (uint32_t s0 = 0; s0 < P.n_src; s0 += 32) {
+      const uint32_t s = s0 + lane;
+      const bool keep = s < P.n_src && (uint64_t)pb_word(P, ti * P.n_src + s) < P.pb_thr;
+      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    if (lane == 0) c.pb_cnt[x] = cnt;
+  }
+}
+
+// one thread per (projection, rank): offsets of the rank's targets (ascending)
+__global__ void pb_scan_kernel(CountedArgs c) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (uint64_t)c.n_pb * c.R) return;
+  const uint32_t q = (uint32_t)(k / c.R), r = (uint32_t)(k - (uint64_t)q * c.R);
+  const DevProj& P = c.projs[c.pb_proj[q]];
+  uint64_t acc = 0;
+  for (uint32_t ti = 0; ti < P.n_tgt; ++ti) {
+    const uint32_t t = P.tgt_first + ti * P.tgt_stride;
+    if (rank_of(t, c.R, c.magic_R) != r) continue;
+    c.pb_off[c.pb_t_first[q] + ti] = acc;
+    acc += c.pb_cnt[c.pb_t_first[q] + ti];
+  }
+  c.pb_tot[k] = acc;
+}
+
+// fixed total over several ranks: regenerate each tile's draws and place them, in draw
+// order within each (rank, projection) block
+__global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs a) {
+  constexpr int NW = 8, ITEMS = kCountTile / 256;
+  __shared__ uint32_t s_w[NW][kMaxCountedRanks / 4 * 4];
+  __shared__ uint32_t s_tbl[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1;
+  for (uint64_t tile = blockIdx.x; tile < c.n_ft_tiles; tile += gridDim.x) {
+    __syncthreads();
+    for (uint32_t i = tid; i < NW * c.R; i += 256) s_w[i / c.R][i % c.R] = 0;
+    const uint32_t q = upper_bound_u64(c.ft_tile_first, c.n_ft, tile) - 1;
+    const uint32_t pid = c.ft_proj[q];
+    const DevProj& P = c.projs[pid];
+    if (P.d_kind == 1)
+      for (uint32_t i = tid; i < P.d_tbl_len; i += 256) s_tbl[i] = a.dtables[P.d_tbl_off + i];
+    __syncthreads();
+    const uint64_t j0 = (tile - c.ft_tile_first[q]) * kCountTile;
+    const uint32_t n = (uint32_t)min((uint64_t)kCountTile, P.N - j0);
+    uint64_t rec[ITEMS];
+    uint32_t rk[ITEMS], rnk[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t idx = warp * 32 * ITEMS + j * 32 + lane;
+      rk[j] = 0xFFFFFFFFu;
+      if (idx < n) {
+        const uint64_t cc = j0 + idx;
+        const uint4 b = philox_stream(cc, P.proj_id, kPurposeSynapse, P.seed);
+        const uint4 bt = philox_stream(cc, P.proj_id, kPurposeFtTarget, P.seed);
+        const uint32_t t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
+        rk[j] = rank_of(t, c.R, c.magic_R);
+        const uint32_t src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
+        rec[j] = make_record(P, a.g, rk[j], cc, src, b.y, s_tbl);
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, rk[j]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (lane == leader && rk[j] != 0xFFFFFFFFu) {
+        old = s_w[warp][rk[j]];
+        s_w[warp][rk[j]] = old + __popc(peers);
+      }
+      old = __shfl_sync(0xffffffffu, old, leader);
+      rnk[j] = old + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (uint32_t r = tid; r < c.R; r += 256) {          // exclusive prefix over warps
+      uint32_t acc = 0;
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t v = s_w[w][r];
+        s_w[w][r] = acc;
+        acc += v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (rk[j] == 0xFFFFFFFFu) continue;
+      const uint64_t pos = c.block_base[(uint64_t)pid * c.R + rk[j]] + c.ft_tile_off[tile * c.R + rk[j]] +
+                           s_w[warp][rk[j]] + rnk[j];
+      if (pos < a.seg_start[rk[j] + 1]) a.rec_a[pos] = rec[j]; else atomicOr(a.err, kErrBounds);
+    }
+  }
+}
+
+// pairwise Bernoulli: one warp per target, kept pairs in source order
+__global__ void __launch_bounds__(256) pb_place_kernel(CountedArgs c, BuildArgs a) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < c.n_pb_targets; x += nwarps) {
+    const uint32_t q = upper_bound_u64(c.pb_t_first, c.n_pb, x) - 1;
+    const uint32_t pid = c.pb_proj[q];
+    const DevProj& P = c.projs[pid];
+    const uint64_t ti = x - c.pb_t_first[q];
+    const uint32_t t = P.tgt_first + (uint32_t)ti * P.tgt_stride;
+    const uint32_t rank = rank_of(t, c.R, c.magic_R);
+    uint64_t pos = c.block_base[(uint64_t)pid * c.R + rank] + c.pb_off[x];
+    const uint64_t end = a.seg_start[rank + 1];
+    for (uint32_t s0 = 0; s0 < P.n_src; s0 += 32) {
+      const uint32_t s = s0 + lane;
+      const uint64_t qq = ti * P.n_src + s;
+      const bool keep = s < P.n_src && (uint64_t)pb_word(P, qq) < P.pb_thr;
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const uint4 b = philox_stream(qq, P.proj_id, kPurposeSynapse, P.seed);
+        const uint32_t src = P.src_first + s * P.src_stride;
+        const uint64_t at = pos + __popc(m & ((1u << lane) - 1));
+        const uint64_t r = make_record(P, a.g, rank, qq, src, b.y, a.dtables + P.d_tbl_off);
+        if (at < end) a.rec_a[at] = r; else atomicOr(a.err, kErrBounds);
+      }
+      pos += __popc(m);
+    }
+  }
+}
+
+cudaError_t launch_counted_count(const CountedArgs& c, cudaStream_t st, int num_sms) {
+  if (c.R > kMaxCountedRanks) return cudaErrorInvalidValue;
+  if (c.n_ft_tiles) {
+    ft_count_kernel<<<(unsigned)std::min<uint64_t>(c.n_ft_tiles, (uint64_t)num_sms * 8), 256, 0, st>>>(c);
+    ft_scan_kernel<<<(unsigned)(((uint64_t)c.n_ft * c.R + 255) / 256), 256, 0, st>>>(c);
+  }
+  if (c.n_pb_targets) {
+    pb_count_kernel<<<(unsigned)std::min<uint64_t>((c.n_pb_targets * 32 + 255) / 256, (uint64_t)num_sms * 16),
+                      256, 0, st>>>(c);
+    pb_scan_kernel<<<(unsigned)(((uint64_t)c.n_pb * c.R + 255) / 256), 256, 0, st>>>(c);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counted_place(const CountedArgs& c, const BuildArgs& a, cudaStream_t st) {
+  if (c.n_ft_tiles)
+    ft_place_kernel<<<(unsigned)std::min<uint64_t>(c.n_ft_tiles, (uint64_t)a.num_sms * 8), 256, 0, st>>>(c, a);
+  if (c.n_pb_targets)
+    pb_place_kernel<<<(unsigned)std::min<uint64_t>((c.n_pb_targets * 32 + 255) / 256, (uint64_t)a.num_sms * 16),
+                      256, 0, st>>>(c, a);
+  return cudaGetLastError();
+}
+
+// per-segment digit histograms of all records (when generation could not fuse them)
+template <int RB>
+__global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
+  constexpr int BINS = 1 << RB;
+  __shared__ uint32_t s_hist[MAX_PASSES][BINS];
+  const uint32_t passes = a.passes;
+  for (int i = threadIdx.x; i < MAX_PASSES * BINS; i += 256) (&s_hist[0][0])[i] = 0;
+  const uint64_t per = (a.n_sort_tiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * per, t1 = min(t0 + per, a.n_sort_tiles);
+  int cur = -1;
+  for (uint64_t tile = t0; tile < t1; ++tile) {
+    const uint32_t seg = upper_bound_u64(a.seg_tile0, a.g.R, tile) - 1;
+    __syncthreads();
+    if ((int)seg != cur) {
+      if (cur >= 0)
+        for (int i = threadIdx.x; i < (int)passes * BINS; i += 256) {
+          const uint32_t v = (&s_hist[0][0])[i];
+          if (v) atomicAdd((unsigned long long*)&a.hist[((uint64_t)cur * passes) * BINS + i], v);
+          (&s_hist[0][0])[i] = 0;
+        }
+      cur = seg;
+    }
+    __syncthreads();
+    const uint64_t base = a.seg_start[seg] + (tile - a.seg_tile0[seg]) * SORT_TILE;
+    const uint64_t end = min(base + SORT_TILE, a.seg_start[seg + 1]);
+    for (uint64_t i = base + threadIdx.x; i < end; i += 256) {
+      const uint64_t kk = a.rec_a[i] >> a.g.cbits;
+#pragma unroll
+      for (int p = 0; p < MAX_PASSES; ++p)
+        if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  if (cur >= 0)
+    for (int i = threadIdx.x; i < (int)passes * BINS; i += 256) {
+      const uint32_t v = (&s_hist[0][0])[i];
+      if (v) atomicAdd((unsigned long long*)&a.hist[((uint64_t)cur * passes) * BINS + i], v);
+    }
+}
+
+cudaError_t launch_histogram(const BuildArgs& a, cudaStream_t st) {
+  if (a.n_sort_tiles == 0 || a.passes == 0) return cudaSuccess;
+  hist_kernel<8><<<(unsigned)std::min<uint64_t>(a.n_sort_tiles, (uint64_t)a.num_sms * 8), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

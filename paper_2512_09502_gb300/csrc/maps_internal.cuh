@@ -9,13 +9,35 @@
 
 namespace snn {
 
+struct RouteArgs {
+  uint32_t R, N, exchange;
+  const uint32_t* rank_off; const uint32_t* M; const uint64_t* rows_off;
+  const uint64_t* tp_ptr; const uint32_t* T; const uint32_t* P; const uint64_t* img_off;
+  const uint64_t* h_pos; const int32_t* I;
+  const uint32_t* step; uint32_t* err;
+  const uint32_t* spk; const uint32_t* n_spk;
+  uint32_t* work; uint32_t* n_work; uint64_t work_cap;
+};
+
 struct MapsState {
+  uint32_t R = 0, N = 0, Mmax = 0;
+  std::vector<uint32_t> M, rank_off;
+  uint32_t* d_M = nullptr; uint32_t* d_rank_off = nullptr;
+  // target side
   uint64_t n_images_total = 0;
-  std::vector<uint64_t> n_img;          // images per rank
-  std::vector<uint64_t> rp_off;         // first entry of each rank's row_ptr in rows
-  uint64_t* rows = nullptr;             // concatenated per-rank row_ptr (absolute)
-  uint32_t* img_gid = nullptr;          // gid of every image row, per rank concatenated
-  std::vector<uint64_t> img_off;        // first image of each rank in img_gid
+  std::vector<uint64_t> n_img, img_first, rows_off, img_off;   // img_off: [R][R+1] by slot
+  uint64_t* d_rows_off = nullptr; uint64_t* d_img_first = nullptr; uint64_t* d_img_off = nullptr;
+  uint64_t* rows = nullptr;             // concatenated per-rank row starts (absolute)
+  uint32_t* img_gid = nullptr;          // gid of every image, rank-major
+  uint32_t* img_s = nullptr;            // its local index on the source rank (R maps)
+  // source side
+  uint64_t* spos = nullptr;             // [R][R][Mmax] prefix positions of S entries
+  std::vector<uint64_t> S_off;          // [R*R+1] start of S_{tau,sigma} at sigma*R+tau
+  uint64_t* d_S_off = nullptr; uint32_t* S_vals = nullptr;
+  uint64_t* tp_ptr = nullptr; uint32_t* T = nullptr; uint32_t* P = nullptr; uint64_t n_tp = 0;
+  uint64_t* h_pos = nullptr; std::vector<uint64_t> h_off; uint64_t* d_h_off = nullptr;
+  uint32_t* H = nullptr; int32_t* I = nullptr; uint64_t n_h = 0;
+  RouteArgs route{};
 };
 
 // accessors of the context (api.cu)
@@ -30,6 +52,7 @@ const std::vector<uint64_t>& ctx_seg_start(snn_ctx* c);
 const std::vector<uint32_t>& ctx_rank_sizes(snn_ctx* c);
 const std::vector<uint32_t>& ctx_rank_off(snn_ctx* c);
 uint64_t* ctx_dense(snn_ctx* c);
+const uint32_t* ctx_dense_off(snn_ctx* c);
 const uint64_t* ctx_dseg_start(snn_ctx* c);
 const float* ctx_scale_src(snn_ctx* c);
 int ctx_num_sms(snn_ctx* c);

@@ -8,6 +8,10 @@
 // model (not stated in the paper) is the exactly integrated iaf_psc_exp of Rotter &
 // Diesmann (1999) with propagators computed in FP64 at calibrate.
 //
+// When every population has tau_syn_ex == tau_syn_in the two receptors obey the same
+// linear dynamics, so one ring and one current (I_ex, holding the sum) give the same
+// membrane potential with half the ring footprint; I_in then stays 0.
+//
 // One step = update_kernel (reads and clears ring slot n, integrates, appends spikes
 // to the per-step delivery list) then deliver_kernel (walks the rows of every listed
 // spike and red.add's the weights into slots n + d); the last deliver CTA to finish
@@ -21,74 +25,92 @@
 namespace snn {
 
 constexpr int UPD_BLOCK = 256;
+constexpr int UPD_ILP = 4;        // neurons per thread per iteration (loads issued together)
 constexpr int DEL_BLOCK = 256;
+constexpr int DEL_ILP = 4;        // events per thread per iteration
+constexpr uint32_t MAX_SMEM_DRIVES = 16;
 
 __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
   __shared__ uint32_t s_tbl[256];
   __shared__ DevPop s_pop[64];
+  __shared__ DevDrive s_dr[MAX_SMEM_DRIVES];
   const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31;
   const uint32_t n = *a.step;
   for (uint32_t i = tid; i < a.poisson_tbl_len && i < 256; i += UPD_BLOCK) s_tbl[i] = a.poisson_tbl[i];
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
-  if (blockIdx.x == 0 && tid == 0) a.n_items[(n + 1) & 1] = 0;   // next step's list
+  for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
+  if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;   // next step's list
   __syncthreads();
-  const uint32_t i = blockIdx.x * UPD_BLOCK + tid;
-  bool spike = false;
-  uint32_t gid = 0;
-  if (i < a.N) {
-    const uint32_t pi = a.pop_of[i];
-    const DevPop P = pi < 64 ? s_pop[pi] : a.pops[pi];
-    gid = a.R == 1 ? i : a.gid_of[i];
-    float V = a.V[i], Iex = a.Iex[i], Iin = a.Iin[i];
-    uint32_t refr = a.refr[i];
-    if (refr == 0) {
-      V = P.P22 * V + P.P21ex * Iex + P.P21in * Iin + P.P20 * P.Ie;
-    } else {
-      --refr;
-    }
-    const uint32_t slot = n & a.ring_mask;
-    float* rex = a.ring + ((uint64_t)slot * 2) * a.N;
-    float* rin = rex + a.N;
-    Iex = P.P11ex * Iex + rex[i];
-    Iin = P.P11in * Iin + rin[i];
-    rex[i] = 0.f;
-    rin[i] = 0.f;
-    for (uint32_t k = 0; k < a.ndrives; ++k) {
-      const DevDrive dr = a.drives[k];
-      if (gid - dr.first < dr.n) {
-        const uint4 b = philox_stream((uint64_t)gid | ((uint64_t)n << 32), dr.idx, kPurposePoisson,
-                                      dr.seed);
-        const uint32_t cnt = upper_bound_u32(s_tbl + dr.tbl_off, dr.tbl_len, b.x);
-        if (dr.weight >= 0.f) Iex += (float)cnt * dr.weight; else Iin += (float)cnt * dr.weight;
+  const uint32_t slot = n & a.ring_mask;
+  float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.N;
+  float* rin = rex + a.N;
+  const uint64_t stride = (uint64_t)gridDim.x * UPD_BLOCK * UPD_ILP;
+  for (uint64_t base = (uint64_t)blockIdx.x * UPD_BLOCK * UPD_ILP; base < a.N; base += stride) {
+    float V[UPD_ILP], Iex[UPD_ILP], Iin[UPD_ILP], in_ex[UPD_ILP], in_in[UPD_ILP];
+    uint32_t refr[UPD_ILP], pi[UPD_ILP];
+#pragma unroll
+    for (int k = 0; k < UPD_ILP; ++k) {
+      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
+      if (i < a.N) {
+        V[k] = a.V[i]; Iex[k] = a.Iex[i]; Iin[k] = a.Iin[i];
+        refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
+        in_ex[k] = rex[i];
+        in_in[k] = a.n_rec == 2 ? rin[i] : 0.f;
       }
     }
-    if (V >= P.Vth) {
-      V = P.Vreset;
-      refr = P.ref_steps;
-      spike = true;
-    }
-    a.V[i] = V;
-    a.Iex[i] = Iex;
-    a.Iin[i] = Iin;
-    a.refr[i] = (uint16_t)refr;
-  }
-  // warp-aggregated append of the step's spikes (delivery items = rows of rank 0 for
-  // one rank, neuron positions for the router otherwise)
-  const uint32_t mask = __ballot_sync(0xffffffffu, spike);
-  if (mask) {
-    const int lane = tid & 31;
-    const int leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&a.n_items[n & 1], __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    const uint32_t off = __popc(mask & ((1u << lane) - 1));
-    if (spike) {
-      a.items[(uint64_t)(n & 1) * a.N + base + off] = i;
-      unsigned long long lb = 0;
-      if (lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
-      lb = __shfl_sync(mask, lb, leader);
-      const unsigned long long slot = lb + off;
-      if (slot < a.log_cap) a.log[slot] = make_uint2(n, gid);
+#pragma unroll
+    for (int k = 0; k < UPD_ILP; ++k) {
+      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
+      bool spike = false;
+      uint32_t gid = 0;
+      if (i < a.N) {
+        const DevPop P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
+        gid = a.R == 1 ? (uint32_t)i : a.gid_of[i];
+        float v = V[k], ie = Iex[k], ii = Iin[k];
+        uint32_t rf = refr[k];
+        if (rf == 0) v = P.P22 * v + P.P21ex * ie + P.P21in * ii + P.P20 * P.Ie;
+        else --rf;
+        ie = P.P11ex * ie + in_ex[k];
+        ii = P.P11in * ii + in_in[k];
+        for (uint32_t q = 0; q < a.ndrives; ++q) {
+          const DevDrive dr = q < MAX_SMEM_DRIVES ? s_dr[q] : a.drives[q];
+          if (gid - dr.first < dr.n) {
+            const uint4 b = philox_stream((uint64_t)gid | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
+            const uint32_t cnt = upper_bound_u32(s_tbl + dr.tbl_off, dr.tbl_len, b.x);
+            if (dr.weight >= 0.f || a.n_rec == 1) ie += (float)cnt * dr.weight; else ii += (float)cnt * dr.weight;
+          }
+        }
+        if (v >= P.Vth) {
+          v = P.Vreset;
+          rf = P.ref_steps;
+          spike = true;
+        }
+        a.V[i] = v;
+        a.Iex[i] = ie;
+        a.Iin[i] = ii;
+        a.refr[i] = (uint16_t)rf;
+        rex[i] = 0.f;
+        if (a.n_rec == 2) rin[i] = 0.f;
+      }
+      // warp-aggregated append of the step's spiking positions (on one rank these are
+      // directly the rows to deliver; with several ranks the router expands them)
+      const uint32_t mask = __ballot_sync(0xffffffffu, spike);
+      if (mask) {
+        const int leader = __ffs(mask) - 1;
+        uint32_t sbase = 0;
+        if ((int)lane == leader) sbase = atomicAdd(&a.n_spk[n & 1], __popc(mask));
+        sbase = __shfl_sync(0xffffffffu, sbase, leader);
+        const uint32_t off = __popc(mask & ((1u << lane) - 1));
+        if (spike) {
+          a.spk[(uint64_t)(n & 1) * a.N + sbase + off] = (uint32_t)i;
+          unsigned long long lb = 0;
+          if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
+          lb = __shfl_sync(mask, lb, leader);
+          const unsigned long long ls = lb + off;
+          if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid);
+        }
+      }
     }
   }
 }
@@ -109,22 +131,48 @@ __device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e) {
 template <typename WT>
 __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT* __restrict__ w) {
   const uint32_t n = *a.step;
-  const uint32_t nitems = a.n_items[n & 1];
-  const uint32_t* items = a.items + (uint64_t)(n & 1) * a.N;
+  const uint32_t nitems = a.n_work[n & 1];
+  const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
   const uint32_t slices = a.slices;
   const uint64_t total = (uint64_t)nitems * slices;
+  float* __restrict__ ring = a.ring;
   for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
     const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
     const uint32_t row = items[si];
-    const uint64_t ra = a.row_ptr[row], rb = a.row_ptr[row + 1];
+    const uint64_t ra = a.rows[row], rb = a.rows[row + 1];
     const uint64_t len = rb - ra;
     const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
     const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
-    for (uint64_t e = lo + threadIdx.x; e < hi; e += DEL_BLOCK) {
-      const float ww = load_w<WT>(w, e) * sc;
-      const uint32_t t = __ldg(a.tgt + e);
-      const uint32_t slot = (n + __ldg(a.d + e)) & a.ring_mask;
-      if (t < a.N) atomicAdd(a.ring + ((uint64_t)slot * 2 + (ww < 0.f ? 1 : 0)) * a.N + t, ww);
+    uint32_t toff = 0;                     // first neuron position of the row's rank
+    if (a.R > 1) {
+      uint32_t l = 0, h = a.R;
+      while (l < h) {
+        const uint32_t mid = (l + h) >> 1;
+        if (a.rows_off[mid] <= row) l = mid + 1; else h = mid;
+      }
+      toff = a.rank_off[l - 1];
+    }
+    for (uint64_t e0 = lo + threadIdx.x; e0 < hi; e0 += (uint64_t)DEL_ILP * DEL_BLOCK) {
+      float ww[DEL_ILP];
+      uint32_t tt[DEL_ILP], dd[DEL_ILP];
+#pragma unroll
+      for (int k = 0; k < DEL_ILP; ++k) {
+        const uint64_t e = e0 + (uint64_t)k * DEL_BLOCK;
+        if (e < hi) {
+          ww[k] = load_w<WT>(w, e) * sc;
+          tt[k] = __ldg(a.tgt + e) + toff;
+          dd[k] = __ldg(a.d + e);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < DEL_ILP; ++k) {
+        const uint64_t e = e0 + (uint64_t)k * DEL_BLOCK;
+        if (e < hi && tt[k] < a.N) {
+          const uint32_t slot = (n + dd[k]) & a.ring_mask;
+          const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
+          atomicAdd(ring + ((uint64_t)slot * a.n_rec + rec) * a.N + tt[k], ww[k]);
+        }
+      }
     }
     if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);
   }
@@ -157,7 +205,9 @@ __global__ void init_state_kernel(SimArgs a, const float* v0) {
 }
 
 cudaError_t launch_update(const SimArgs& a, cudaStream_t st) {
-  update_kernel<<<(a.N + UPD_BLOCK - 1) / UPD_BLOCK, UPD_BLOCK, 0, st>>>(a);
+  const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_ILP - 1) / (UPD_BLOCK * UPD_ILP);
+  const unsigned grid = (unsigned)(need < a.update_grid ? need : a.update_grid);
+  update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -12,17 +12,22 @@ struct SimArgs {
   const DevPop* pops; uint32_t npops;
   const DevDrive* drives; uint32_t ndrives;
   const uint32_t* poisson_tbl; uint32_t poisson_tbl_len;
-  float* ring; uint32_t ring_mask;            // [D][2][N]
+  float* ring; uint32_t ring_mask;            // [D][n_rec][N]
+  uint32_t n_rec;                             // 2 receptors, or 1 when tau_ex == tau_in
   uint32_t* step;                             // device step counter
-  uint32_t* n_items; uint32_t* items;         // [2] counts, [2][N] per-step lists
+  uint32_t* n_spk; uint32_t* spk;             // [2] counts, [2][N] spiking positions
+  uint32_t* n_work; uint32_t* work;           // [2] counts, [2][stride] rows to deliver
+  uint64_t work_stride;
   unsigned long long* n_logged; uint2* log; unsigned long long log_cap;
   unsigned long long* n_events; unsigned long long* n_spikes_total;
   uint32_t* done;
-  const uint64_t* row_ptr;                    // rows of rank 0 (one rank)
+  const uint64_t* rows;                       // row starts (absolute); one rank: gid rows
+  const uint64_t* rows_off;                   // [R+1] first row of each rank (R > 1)
+  const uint32_t* rank_off;                   // [R+1] first neuron position of each rank
   const uint32_t* tgt; const void* w; const uint8_t* d; uint32_t w_format;
   const float* row_scale;                     // per row (fp16 format) or null
-  uint32_t slices;
-  uint32_t deliver_grid;
+  uint32_t slices;                            // slices of one row (several CTAs per row)
+  uint32_t deliver_grid, update_grid;
 };
 
 cudaError_t launch_update(const SimArgs& a, cudaStream_t st);

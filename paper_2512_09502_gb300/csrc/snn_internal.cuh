@@ -161,7 +161,37 @@ struct BuildArgs {
   const uint32_t* dense_off;  // [R][R]
   const float* row_scale_src; // per source gid (fp16 format) or null
   int num_sms;
+  uint32_t fuse_hist;         // generation accumulates the sort histograms itself
 };
+
+// counted generation (fixed total over several ranks; pairwise Bernoulli): the
+// records of such a projection land in (rank, projection) blocks whose sizes are
+// counted first, so their placement needs a count / scan / place sequence.
+struct CountedArgs {
+  const DevProj* projs;
+  uint32_t R; uint64_t magic_R;
+  // fixed total over several ranks: tiles of kCountTile draws
+  const uint32_t* ft_proj;        // [n_ft] projection ids
+  const uint64_t* ft_tile_first;  // [n_ft + 1]
+  uint32_t n_ft; uint64_t n_ft_tiles;
+  uint32_t* ft_tile_cnt;          // [n_ft_tiles][R]
+  uint64_t* ft_tile_off;          // [n_ft_tiles][R]
+  uint64_t* ft_tot;               // [n_ft][R]
+  // pairwise Bernoulli: one counter per target
+  const uint32_t* pb_proj;        // [n_pb]
+  const uint64_t* pb_t_first;     // [n_pb + 1] first target slot of each projection
+  uint32_t n_pb; uint64_t n_pb_targets;
+  uint32_t* pb_cnt;               // [n_pb_targets] by projection-local target index
+  uint64_t* pb_off;               // [n_pb_targets] offset of the target within its block
+  uint64_t* pb_tot;               // [n_pb][R]
+  const uint64_t* block_base;     // [nproj][R] absolute first record of block (p, rank)
+};
+constexpr uint32_t kCountTile = 4096;
+constexpr uint32_t kMaxCountedRanks = 1024;
+
+cudaError_t launch_counted_count(const CountedArgs& c, cudaStream_t st, int num_sms);
+cudaError_t launch_counted_place(const CountedArgs& c, const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_histogram(const BuildArgs& a, cudaStream_t st);
 
 cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st);

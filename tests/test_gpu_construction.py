@@ -93,3 +93,11 @@ def test_full_size_sampled_parity():
                 np.testing.assert_array_equal(d[m].astype(np.int64), one["d"][order])
                 assert f32_ulp_distance(w[m], one["w"][order].astype(np.float32)).max() <= 4
     ctx.destroy()
+
+
+def test_multi_area_batched_blocks():
+    """Multi-area stand-in (8 areas, 64 fixed-total intra blocks per area plus
+    fixed in-degree inter-area blocks, uneven sizes) built in one generation launch."""
+    net = wl.multi_area(seed=1234, n_areas=8, area_mean=400.0)
+    assert len(net.projections) > 8 * 64
+    _check(net)

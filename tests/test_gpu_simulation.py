@@ -15,10 +15,10 @@ def lib():
     return ensure_lib()
 
 
-def _oracle_sim(net, ref_rank, weights32=True):
+def _oracle_sim(net, ref_rank, weights32=True, stored_fp32=False):
     w = ref_rank["w"].astype(np.float32).astype(np.float64) if weights32 else ref_rank["w"]
     D = on.ring_slots_for(oc.max_delay(net))
-    return on.Simulator(net, ref_rank["row_ptr"], ref_rank["tgt"], ref_rank["d"], w, D)
+    return on.Simulator(net, ref_rank["row_ptr"], ref_rank["tgt"], ref_rank["d"], w, D, stored_fp32=stored_fp32)
 
 
 def test_membrane_within_1e4_mv_over_100_steps():
@@ -34,10 +34,28 @@ def test_membrane_within_1e4_mv_over_100_steps():
         sim.step()
         V, Iex, Iin = ctx.get_state(0, net.n_neurons)
         worst = max(worst, float(np.max(np.abs(V - sim.V))))
-        np.testing.assert_allclose(Iex, sim.Iex, rtol=1e-5, atol=1e-3)
+        # equal tau_syn: one shared current holds I_ex + I_in
+        np.testing.assert_allclose(Iex + Iin, sim.Iex + sim.Iin, rtol=1e-5, atol=1e-3)
     assert worst <= 1e-4, worst
     st, gid = ctx.get_spikes()
     assert len(st) == 0 or st.max() < 100
+
+
+def test_two_receptor_path():
+    """Different synaptic time constants keep separate ex / in rings and currents."""
+    p = wl.NeuronParams(tau_syn_ex=0.5, tau_syn_in=2.0)
+    net = wl.balanced(1600, 400, 80, 20, wl.DELAY_NORMAL, seed=5, params=p, drive_rate_hz=10200.0)
+    ctx = gpu_build(net, use_graph=False)
+    _, ref = oracle_layout(net)
+    sim = _oracle_sim(net, ref["ranks"][0])
+    for _ in range(100):
+        ctx.simulate(1)
+        sim.step()
+    V, Iex, Iin = ctx.get_state(0, net.n_neurons)
+    assert np.max(np.abs(V - sim.V)) <= 1e-4
+    np.testing.assert_allclose(Iex, sim.Iex, rtol=1e-5, atol=1e-3)
+    np.testing.assert_allclose(Iin, sim.Iin, rtol=1e-5, atol=1e-3)
+    assert np.min(Iin) < -1.0
 
 
 def test_graph_and_stream_paths_agree():
@@ -63,7 +81,8 @@ def test_population_rates_within_2_percent():
     ctx.simulate(steps)
     st, gid = ctx.get_spikes()
     _, ref = oracle_layout(net)
-    sim = _oracle_sim(net, ref["ranks"][0])
+    # propagators as the method stores them (FP64 -> FP32 once); see oracle/neuron.py
+    sim = _oracle_sim(net, ref["ranks"][0], stored_fp32=True)
     spikes, _ = sim.run(steps)
     o = np.array([g for _, g in spikes])
     T = steps * net.dt / 1000.0

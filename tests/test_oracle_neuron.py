@@ -84,3 +84,14 @@ def test_delivery_slot_and_receptor():
     assert sim.ring[(6 + 3) % 8, 0, 1] == 10.0
     assert sim.ring[(6 + 5) % 8, 1, 1] == -4.0
     assert np.count_nonzero(sim.ring) == 2
+
+
+def test_stored_fp32_propagators_round_once():
+    p = wl.BALANCED_PARAMS
+    net = _one_neuron_net(p)
+    a = on.Simulator(net, np.array([0, 0]), np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), 8)
+    b = on.Simulator(net, np.array([0, 0]), np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), 8,
+                     stored_fp32=True)
+    for k in ["P22", "P20", "P11_ex", "P21_ex"]:
+        assert b.c[k][0] == float(np.float32(a.c[k][0]))
+        assert abs(b.c[k][0] - a.c[k][0]) <= 2 ** -24 * abs(a.c[k][0])
