@@ -273,7 +273,7 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
   if (!(config->dt_ms > 0) || config->n_ranks < 1 || config->weight_format < 0 ||
       config->weight_format > 2 || (config->exchange != 0 && config->exchange != 1))
     return SNN_EINVAL;
-  if (config->radix_bits != 0 && config->radix_bits != 8) return SNN_EINVAL;
+  if (config->radix_bits != 0 && config->radix_bits != 8 && config->radix_bits != 9) return SNN_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
     cudaGetLastError();

@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
 cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st) {
   if (a.n_gen_tiles == 0) return cudaSuccess;
   const uint64_t grid = std::min<uint64_t>(a.n_gen_tiles, (uint64_t)a.num_sms * 8);
-  if (a.radix_bits != 8) return cudaErrorInvalidValue;
-  gen_kernel<8><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
+  if (a.radix_bits == 8) gen_kernel<8><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
+  else if (a.radix_bits == 9) gen_kernel<9><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -174,66 +175,99 @@ __device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
 }
 
 template <int RB>
-__global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_t pass,
+struct SortSmem {
+  static constexpr int BINS = 1 << RB;
+  static constexpr int NW = SORT_BLOCK / 32;
+  uint64_t stage[SORT_TILE];
+  uint64_t gbase[BINS];
+  uint32_t whist[NW][BINS];
+  uint32_t binstart[BINS];
+  uint32_t wsum[NW];
+  uint32_t tile;
+};
+
+// Exclusive prefix of bin b over the predecessor tiles of this segment: sum the
+// aggregates of earlier tiles until one carries an inclusive prefix.  Eight status
+// words are requested per round trip; a word that is not ready yet is polled with a
+// bounded wait (a global error flag short-cuts every other wait once one gave up).
+__device__ __forceinline__ uint64_t look_back(const BuildArgs& a, uint64_t tile, uint64_t first_tile,
+                                              uint32_t b, uint32_t bins, uint32_t epoch) {
+  constexpr int W = 8;
+  const uint64_t ep = (uint64_t)(epoch & 0xFFFF) << 46;
+  uint64_t excl = 0;
+  uint64_t k = tile - 1;                    // tile > first_tile here
+  while (true) {
+    uint64_t st[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      st[w] = (k >= first_tile + w) ? ld_status(a.status + (k - w) * bins + b) : 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint64_t s = st[w];
+      const uint64_t* sp = a.status + (k - w) * bins + b;
+      uint32_t spins = 0;
+      while (((s >> 62) == 0) || (((s >> 46) & 0xFFFF) != (epoch & 0xFFFF))) {
+        if (++spins > SPIN_LIMIT || (*(volatile uint32_t*)a.err & kErrTimeout)) {
+          atomicOr(a.err, kErrTimeout);
+          s = ST_INC | ep;
+          break;
+        }
+        __nanosleep(32);
+        s = ld_status(sp);
+      }
+      excl += s & ST_VAL;
+      if ((s >> 62) == 2) return excl;      // the segment's first tile is always inclusive
+    }
+    k -= W;
+  }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint32_t pass,
                                                              const uint64_t* __restrict__ in,
                                                              uint64_t* __restrict__ out,
                                                              uint32_t epoch) {
   constexpr int BINS = 1 << RB;
   constexpr int NW = SORT_BLOCK / 32;
   constexpr int BPT = BINS >= SORT_BLOCK ? BINS / SORT_BLOCK : 1;   // bins per thread
-  __shared__ uint32_t s_whist[NW][BINS];
-  __shared__ uint64_t s_stage[SORT_TILE];
-  __shared__ uint32_t s_binstart[BINS];
-  __shared__ uint64_t s_gbase[BINS];
-  __shared__ uint32_t s_wsum[NW];
-  __shared__ uint32_t s_tile;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem<RB>& sm = *reinterpret_cast<SortSmem<RB>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  if (tid == 0) s_tile = atomicAdd(&a.counters[pass], 1u);
-  for (int i = tid; i < NW * BINS; i += SORT_BLOCK) (&s_whist[0][0])[i] = 0;
+  if (tid == 0) sm.tile = atomicAdd(&a.counters[pass], 1u);
+  for (int i = tid; i < NW * BINS; i += SORT_BLOCK) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
-  const uint64_t tile = s_tile;
+  const uint64_t tile = sm.tile;
   if (tile >= a.n_sort_tiles) return;
 
-  // segment of this tile
-  uint32_t lo = 0, hi = a.g.R;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (a.seg_tile0[mid] <= tile) lo = mid + 1; else hi = mid;
-  }
-  const uint32_t seg = lo - 1;
-  const uint64_t tile_in_seg = tile - a.seg_tile0[seg];
-  const uint64_t base = a.seg_start[seg] + tile_in_seg * SORT_TILE;
-  const uint32_t n = (uint32_t)min((uint64_t)SORT_TILE, a.seg_start[seg + 1] - base);
+  const uint32_t seg = upper_bound_u64(a.seg_tile0, a.g.R, tile) - 1;
+  const uint64_t first_tile = a.seg_tile0[seg];
+  const uint64_t base = a.seg_start[seg] + (tile - first_tile) * SORT_TILE;
+  const uint64_t seg_end = a.seg_start[seg + 1];
+  const uint32_t n = (uint32_t)min((uint64_t)SORT_TILE, seg_end - base);
   const uint32_t shift = a.g.cbits + pass * RB;
   const uint32_t dbits = min((uint32_t)RB, a.g.key_bits - pass * RB);
   const uint64_t dmask = (1ull << dbits) - 1;
 
   uint64_t rec[SORT_ITEMS];
-  uint32_t dig[SORT_ITEMS];
   uint32_t rnk[SORT_ITEMS];
   const uint32_t wbase = warp * 32 * SORT_ITEMS;
 #pragma unroll
   for (int j = 0; j < SORT_ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
-    if (idx < n) {
-      rec[j] = in[base + idx];
-      dig[j] = (uint32_t)((rec[j] >> shift) & dmask);
-    } else {
-      rec[j] = 0;
-      dig[j] = BINS;   // padding: ranked among itself, never placed
-    }
+    rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
   const uint32_t lt = (1u << lane) - 1;
 #pragma unroll
   for (int j = 0; j < SORT_ITEMS; ++j) {
-    const uint32_t d = dig[j];
+    const uint32_t idx = wbase + j * 32 + lane;
+    const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
     if (lane == leader && d < BINS) {
-      old = s_whist[warp][d];
-      s_whist[warp][d] = old + __popc(peers);
+      old = sm.whist[warp][d];
+      sm.whist[warp][d] = old + __popc(peers);
     }
     old = __shfl_sync(0xffffffffu, old, leader);
     rnk[j] = old + __popc(peers & lt);
@@ -241,7 +275,6 @@ __global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_
   }
   __syncthreads();
 
-  // per bin: exclusive prefix over warps, tile count, look-back, global base
   uint32_t tot[BPT];
   uint32_t tsum = 0;
 #pragma unroll
@@ -251,15 +284,15 @@ __global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_
     if (b < BINS) {
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
-        const uint32_t c = s_whist[w][b];
-        s_whist[w][b] = t;
+        const uint32_t c = sm.whist[w][b];
+        sm.whist[w][b] = t;
         t += c;
       }
     }
     tot[q] = t;
     tsum += t;
   }
-  const bool first = tile_in_seg == 0;
+  const bool first = tile == first_tile;
   const uint64_t ep = (uint64_t)(epoch & 0xFFFF) << 46;
   uint64_t* strow = a.status + tile * BINS;
 #pragma unroll
@@ -273,28 +306,10 @@ __global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_
     if (b >= BINS) continue;
     uint64_t excl = 0;
     if (!first) {
-      uint64_t k = tile - 1;
-      while (true) {
-        const uint64_t* sp = a.status + k * BINS + b;
-        uint64_t s = ld_status(sp);
-        uint32_t spins = 0;
-        while (((s >> 62) == 0) || (((s >> 46) & 0xFFFF) != (epoch & 0xFFFF))) {
-          // bounded wait; give up at once when another wait has already timed out
-          if (++spins > SPIN_LIMIT || (*(volatile uint32_t*)a.err & kErrTimeout)) {
-            atomicOr(a.err, kErrTimeout);
-            s = ST_INC | ep;
-            break;
-          }
-          __nanosleep(32);
-          s = ld_status(sp);
-        }
-        excl += s & ST_VAL;
-        if ((s >> 62) == 2) break;
-        --k;
-      }
+      excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
       st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
     }
-    s_gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * BINS + b] + excl;
+    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * BINS + b] + excl;
   }
 
   // tile-local exclusive scan of the bin counts (thread-contiguous bins)
@@ -304,40 +319,52 @@ __global__ void __launch_bounds__(SORT_BLOCK) onesweep_pass(BuildArgs a, uint32_
     const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
-  if (lane == 31) s_wsum[warp] = incl;
+  if (lane == 31) sm.wsum[warp] = incl;
   __syncthreads();
   uint32_t woff = 0;
-  for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+  for (int w = 0; w < warp; ++w) woff += sm.wsum[w];
   uint32_t run = woff + incl - tsum;
 #pragma unroll
   for (int q = 0; q < BPT; ++q) {
     const int b = tid * BPT + q;
-    if (b < BINS) s_binstart[b] = run;
+    if (b < BINS) sm.binstart[b] = run;
     run += tot[q];
   }
   __syncthreads();
 
 #pragma unroll
   for (int j = 0; j < SORT_ITEMS; ++j) {
-    const uint32_t d = dig[j];
-    if (d < BINS) s_stage[s_binstart[d] + s_whist[warp][d] + rnk[j]] = rec[j];
+    const uint32_t idx = wbase + j * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (uint32_t)((rec[j] >> shift) & dmask);
+      sm.stage[sm.binstart[d] + sm.whist[warp][d] + rnk[j]] = rec[j];
+    }
   }
   __syncthreads();
-  const uint64_t seg_end = a.seg_start[seg + 1];
   for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
-    const uint64_t r = s_stage[k];
+    const uint64_t r = sm.stage[k];
     const uint32_t d = (uint32_t)((r >> shift) & dmask);
-    const uint64_t gpos = s_gbase[d] + (k - s_binstart[d]);
+    const uint64_t gpos = sm.gbase[d] + (k - sm.binstart[d]);
     if (gpos < seg_end) out[gpos] = r; else atomicOr(a.err, kErrBounds);
   }
+}
+
+template <int RB>
+static cudaError_t sort_pass_rb(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
+                                uint32_t epoch, cudaStream_t st) {
+  const size_t smem = sizeof(SortSmem<RB>);
+  cudaError_t e = cudaFuncSetAttribute(onesweep_pass<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  onesweep_pass<RB><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, smem, st>>>(a, pass, in, out, epoch);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                              uint32_t epoch, cudaStream_t st) {
   if (a.n_sort_tiles == 0) return cudaSuccess;
-  if (a.radix_bits != 8) return cudaErrorInvalidValue;
-  onesweep_pass<8><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, 0, st>>>(a, pass, in, out, epoch);
-  return cudaGetLastError();
+  if (a.radix_bits == 8) return sort_pass_rb<8>(a, pass, in, out, epoch, st);
+  if (a.radix_bits == 9) return sort_pass_rb<9>(a, pass, in, out, epoch, st);
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -598,7 +625,10 @@ __global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
 
 cudaError_t launch_histogram(const BuildArgs& a, cudaStream_t st) {
   if (a.n_sort_tiles == 0 || a.passes == 0) return cudaSuccess;
-  hist_kernel<8><<<(unsigned)std::min<uint64_t>(a.n_sort_tiles, (uint64_t)a.num_sms * 8), 256, 0, st>>>(a);
+  const unsigned grid = (unsigned)std::min<uint64_t>(a.n_sort_tiles, (uint64_t)a.num_sms * 8);
+  if (a.radix_bits == 8) hist_kernel<8><<<grid, 256, 0, st>>>(a);
+  else if (a.radix_bits == 9) hist_kernel<9><<<grid, 256, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -115,17 +115,51 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
   }
 }
 
+// Streaming loads of the connection arrays with an L2 evict-first policy, and ring
+// reductions with evict-last: each connection is read once per spike, while the ring's
+// active slots are reused by every step, so the ring should keep the L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const void* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u16(const void* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u8(const void* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void red_add_keep(float* p, float v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(p), "f"(v), "l"(pol) : "memory");
+}
+
 template <typename WT>
-__device__ __forceinline__ float load_w(const WT* w, uint64_t e);
+__device__ __forceinline__ float load_w(const WT* w, uint64_t e, uint64_t pol);
 template <>
-__device__ __forceinline__ float load_w<float>(const float* w, uint64_t e) { return __ldg(w + e); }
-template <>
-__device__ __forceinline__ float load_w<__nv_bfloat16>(const __nv_bfloat16* w, uint64_t e) {
-  return __bfloat162float(w[e]);
+__device__ __forceinline__ float load_w<float>(const float* w, uint64_t e, uint64_t pol) {
+  return __uint_as_float(ld_stream_u32(w + e, pol));
 }
 template <>
-__device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e) {
-  return __half2float(w[e]);
+__device__ __forceinline__ float load_w<__nv_bfloat16>(const __nv_bfloat16* w, uint64_t e, uint64_t pol) {
+  return __uint_as_float(ld_stream_u16(w + e, pol) << 16);
+}
+template <>
+__device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e, uint64_t pol) {
+  return __half2float(__ushort_as_half((unsigned short)ld_stream_u16(w + e, pol)));
 }
 
 template <typename WT>
@@ -136,6 +170,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
   const uint32_t slices = a.slices;
   const uint64_t total = (uint64_t)nitems * slices;
   float* __restrict__ ring = a.ring;
+  const uint64_t pol_stream = policy_evict_first(), pol_ring = policy_evict_last();
   for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
     const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
     const uint32_t row = items[si];
@@ -159,9 +194,9 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
       for (int k = 0; k < DEL_ILP; ++k) {
         const uint64_t e = e0 + (uint64_t)k * DEL_BLOCK;
         if (e < hi) {
-          ww[k] = load_w<WT>(w, e) * sc;
-          tt[k] = __ldg(a.tgt + e) + toff;
-          dd[k] = __ldg(a.d + e);
+          ww[k] = load_w<WT>(w, e, pol_stream) * sc;
+          tt[k] = ld_stream_u32(a.tgt + e, pol_stream) + toff;
+          dd[k] = ld_stream_u8(a.d + e, pol_stream);
         }
       }
 #pragma unroll
@@ -170,7 +205,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
         if (e < hi && tt[k] < a.N) {
           const uint32_t slot = (n + dd[k]) & a.ring_mask;
           const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
-          atomicAdd(ring + ((uint64_t)slot * a.n_rec + rec) * a.N + tt[k], ww[k]);
+          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.N + tt[k], ww[k], pol_ring);
         }
       }
     }

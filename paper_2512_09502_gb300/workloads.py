@@ -137,12 +137,14 @@ BALANCED_PARAMS = NeuronParams(tau_m=10.0, C_m=250.0, tau_syn_ex=0.5, tau_syn_in
 
 def balanced(n_e: int, n_i: int, k_e: int, k_i: int, delay: Dist, *, seed: int = 1234,
              name: str = "balanced", params: NeuronParams = BALANCED_PARAMS,
-             drive_rate_hz: float = 8000.0, n_ranks: int = 1) -> Network:
+             drive_rate_hz: float = 8000.0, n_ranks: int = 1, j_scale: float = 1.0) -> Network:
     """Two-population balanced random network with fixed in-degree (K_E from the E
-    population, K_I from the I population onto every neuron)."""
+    population, K_I from the I population onto every neuron); ``j_scale`` scales the
+    recurrent weights (not the drive)."""
     n = n_e + n_i
-    w_e = Dist(W_NORMAL_SIGN, J_E, 0.1 * J_E)
-    w_i = Dist(W_NORMAL_SIGN, -G_INH * J_E, 0.1 * G_INH * J_E)
+    je = J_E * j_scale
+    w_e = Dist(W_NORMAL_SIGN, je, 0.1 * je)
+    w_i = Dist(W_NORMAL_SIGN, -G_INH * je, 0.1 * G_INH * je)
     projs = [
         Projection(0, n_e, 0, n, Rule(RULE_FIXED_INDEGREE, k_e), w_e, delay, seed),
         Projection(n_e, n_i, 0, n, Rule(RULE_FIXED_INDEGREE, k_i), w_i, delay, seed),
