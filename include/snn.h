@@ -235,6 +235,43 @@ int snn_get_delay_table(snn_ctx* ctx, uint32_t proj_id, uint32_t* host_thr, uint
 
 int snn_stats(snn_ctx* ctx, snn_stats_t* out);
 
+/* ---- allocation-free construction ----------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot
+ * call cudaMalloc (a host application that owns all device memory under a fixed
+ * budget, e.g. a simulator embedding this library as a plugin, or a loop that must
+ * never reach the allocator).
+ *
+ * Builds the source-sorted connections of ONE projection between neurons
+ * [0, n_neurons) on one logical rank -- exactly what snn_calibrate builds for a
+ * context with n_ranks = 1, one population of n_neurons and this single projection
+ * (projection id 0), with fp32 weights -- into caller-owned DEVICE buffers:
+ *   dev_row_ptr  uint64[n_neurons + 1]  row starts (row = source gid)
+ *   dev_tgt      uint32[syn_cap]        target gid
+ *   dev_w        float[syn_cap]         weight (pA)
+ *   dev_d        uint8[syn_cap]         delay (steps)
+ * *n_syn (host) receives the synapse count.  Rules: fixed in-degree or fixed total.
+ * Work is issued on `cuda_stream` (a cudaStream_t) and synchronised before return.
+ *
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library routine.
+ * Intermediate data live in a file-scope __device__ scratch array of fixed size,
+ * held by every GPU that loads the library until the process exits (about 16.5 MB).
+ * The limit: at most SNN_NOALLOC_MAX_SYNAPSES synapses per call; larger requests
+ * return SNN_EINVAL.  The first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array, which keeps the previous
+ * call's contents (the call clears what must start at zero): calls that overlap on
+ * the GPU (concurrent streams or threads on one device) race and must be serialised
+ * by the caller.  Errors: EINVAL (bad arguments or over the limit), EOVERFLOW
+ * (syn_cap too small, *n_syn set), ETIMEOUT / ECUDA; a message goes to host_errmsg
+ * (may be NULL). */
+#define SNN_NOALLOC_MAX_SYNAPSES 1048576ull
+int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first, uint32_t n_src,
+                               uint32_t tgt_first, uint32_t n_tgt, const snn_rule* rule,
+                               const snn_dist* weight, const snn_dist* delay, uint64_t seed,
+                               double dt_ms, uint64_t* dev_row_ptr, uint32_t* dev_tgt,
+                               float* dev_w, uint8_t* dev_d, uint64_t syn_cap, uint64_t* n_syn,
+                               void* cuda_stream, char* host_errmsg, size_t errmsg_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsnn.so")
-SOURCES = ["api.cu", "build.cu", "sim.cu", "maps.cu"]
+SOURCES = ["api.cu", "build.cu", "sim.cu", "maps.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

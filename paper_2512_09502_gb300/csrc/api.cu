@@ -1067,8 +1067,13 @@ void snn_destroy(snn_ctx* c) {
 
 }  // extern "C"
 
-// ---- helpers shared with maps.cu (C++ linkage) ----
+// ---- helpers shared with maps.cu and noalloc.cu (C++ linkage) ----
 namespace snn {
+int host_delay_table(double mean, double sd, double lo, double dt, uint32_t* s_min,
+                     std::vector<uint32_t>* thr) {
+  return delay_table(mean, sd, lo, dt, s_min, thr);
+}
+uint32_t host_const_delay_steps(double d, double dt) { return const_delay_steps(d, dt); }
 void* ctx_alloc(snn_ctx* c, size_t bytes) { return dalloc(c, bytes); }
 void ctx_free(snn_ctx* c, void* p) { dfree(c, p); }
 int ctx_fail(snn_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
