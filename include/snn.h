@@ -99,6 +99,8 @@ typedef struct snn_config {
   int32_t device;              /* CUDA device ordinal                                  */
   int32_t profile_kernels;     /* time every update / deliver launch with CUDA events
                                   (no graph then); results in snn_stats_t              */
+  int32_t sort_items;          /* records per thread of a sort tile: 8, 12, 16; 0 = tuned */
+  int32_t deliver_ctas_per_sm; /* delivery grid = SMs x this (1..32); 0 = tuned          */
 } snn_config;
 
 /* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in

@@ -44,7 +44,7 @@ class snn_config(C.Structure):
     _fields_ = [("dt_ms", C.c_double), ("n_ranks", C.c_uint32), ("weight_format", C.c_int32),
                 ("exchange", C.c_int32), ("use_graph", C.c_int32),
                 ("spike_log_capacity", C.c_uint64), ("radix_bits", C.c_int32), ("device", C.c_int32),
-                ("profile_kernels", C.c_int32)]
+                ("profile_kernels", C.c_int32), ("sort_items", C.c_int32), ("deliver_ctas_per_sm", C.c_int32)]
 
 
 class snn_iaf_psc_exp_params(C.Structure):
@@ -161,11 +161,12 @@ class Context:
     def __init__(self, *, dt: float = 0.1, n_ranks: int = 1, weight_format: str = "f32",
                  exchange: str = "p2p", use_graph: bool = True, spike_log_capacity: int = 0,
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
-                 stream: Optional[int] = None, profile_kernels: bool = False):
+                 stream: Optional[int] = None, profile_kernels: bool = False, sort_items: int = 0,
+                 deliver_ctas_per_sm: int = 0):
         self.lib = load()
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
-                         1 if profile_kernels else 0)
+                         1 if profile_kernels else 0, sort_items, deliver_ctas_per_sm)
         self._allocator = allocator
         h = C.c_void_p()
         rc = self.lib.snn_create(C.byref(cfg), C.byref(allocator.struct) if allocator else None,

@@ -273,7 +273,12 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
   if (!(config->dt_ms > 0) || config->n_ranks < 1 || config->weight_format < 0 ||
       config->weight_format > 2 || (config->exchange != 0 && config->exchange != 1))
     return SNN_EINVAL;
-  if (config->radix_bits != 0 && config->radix_bits != 8 && config->radix_bits != 9) return SNN_EINVAL;
+  {
+    const uint32_t rb = config->radix_bits ? (uint32_t)config->radix_bits : 8u;
+    const uint32_t it = config->sort_items ? (uint32_t)config->sort_items : 16u;
+    if (!sort_config_supported(rb, it)) return SNN_EINVAL;
+    if (config->deliver_ctas_per_sm < 0 || config->deliver_ctas_per_sm > 32) return SNN_EINVAL;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
     cudaGetLastError();
@@ -283,6 +288,8 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
   snn_ctx* c = new snn_ctx();
   c->cfg = *config;
   if (c->cfg.radix_bits == 0) c->cfg.radix_bits = 8;
+  if (c->cfg.sort_items == 0) c->cfg.sort_items = 16;
+  if (c->cfg.deliver_ctas_per_sm == 0) c->cfg.deliver_ctas_per_sm = 8;
   if (alloc) c->alloc = *alloc;
   c->st = (cudaStream_t)cuda_stream;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, config->device);
@@ -547,7 +554,7 @@ int snn_calibrate(snn_ctx* c) {
   c->seg_start[R] = pos;
   const uint64_t E = pos;
   c->E = E;
-  const uint64_t SORT_TILE = sort_tile_items(RB);
+  const uint64_t SORT_TILE = sort_tile_items((uint32_t)c->cfg.sort_items);
   std::vector<uint64_t> seg_tile0(R + 1, 0);
   for (uint32_t t = 0; t < R; ++t)
     seg_tile0[t + 1] = seg_tile0[t] + (c->seg_start[t + 1] - c->seg_start[t] + SORT_TILE - 1) / SORT_TILE;
@@ -602,6 +609,7 @@ int snn_calibrate(snn_ctx* c) {
   a.n_sort_tiles = n_sort_tiles; a.cbase_sorted = d_cbase; a.num_sms = c->num_sms;
   a.dense_off = c->d_dense_off;
   a.fuse_hist = counted ? 0u : 1u;
+  a.sort_items = (uint32_t)c->cfg.sort_items;
 
   CK(launch_generate(a, c->st));
   c->stats.kernel_launches += tiles ? 1 : 0;
@@ -735,13 +743,11 @@ int snn_calibrate(snn_ctx* c) {
   AL(s.n_logged, 1, "log count");
   AL(s.n_events, 1, "event count");
   AL(s.n_spikes_total, 1, "spike count");
-  AL(s.done, 1, "done ticket");
   CK(cudaMemsetAsync(s.step, 0, 4, c->st));
   CK(cudaMemsetAsync(s.n_spk, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_logged, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_events, 0, 8, c->st));
   CK(cudaMemsetAsync(s.n_spikes_total, 0, 8, c->st));
-  CK(cudaMemsetAsync(s.done, 0, 4, c->st));
   s.log_cap = c->cfg.spike_log_capacity;
   if (s.log_cap) AL(s.log, s.log_cap, "spike log");
   s.rows = c->d_dense;
@@ -752,7 +758,7 @@ int snn_calibrate(snn_ctx* c) {
     const double avg = E ? (double)E / std::max<uint64_t>(1, (uint64_t)N) : 0.0;
     s.slices = (uint32_t)std::min(64.0, std::max(1.0, std::ceil(avg / 1024.0)));
   }
-  s.deliver_grid = (uint32_t)c->num_sms * 8;
+  s.deliver_grid = (uint32_t)c->num_sms * (uint32_t)c->cfg.deliver_ctas_per_sm;
   s.update_grid = (uint32_t)c->num_sms * 8;
   if (R > 1) {
     int rc = setup_routing(c);
@@ -793,25 +799,24 @@ int snn_calibrate(snn_ctx* c) {
 // ---------------------------------------------------------------------------
 static int run_steps(snn_ctx* c, uint32_t steps) {
   SimArgs& s = c->sim;
-  if (c->cfg.n_ranks > 1) {
-    for (uint32_t k = 0; k < steps; ++k) {
-      CK(launch_update(s, c->st));
-      CK(launch_route(c));
-      CK(launch_deliver(s, c->st));
-    }
-    if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * (2 + route_kernels_per_step(c));
-    return SNN_OK;
-  }
-  if (c->cfg.profile_kernels && !c->capturing) {
-    std::vector<cudaEvent_t> evs(3 * (size_t)steps);
+  if (steps == 0) return SNN_OK;
+  const bool routed = c->cfg.n_ranks > 1;
+  const bool profile = c->cfg.profile_kernels && !c->capturing;
+  std::vector<cudaEvent_t> evs;
+  if (profile) {
+    evs.resize(3 * (size_t)steps);
     for (auto& e : evs) CK(cudaEventCreate(&e));
-    for (uint32_t k = 0; k < steps; ++k) {
-      CK(cudaEventRecord(evs[3 * k], c->st));
-      CK(launch_update(s, c->st));
-      CK(cudaEventRecord(evs[3 * k + 1], c->st));
-      CK(launch_deliver(s, c->st));
-      CK(cudaEventRecord(evs[3 * k + 2], c->st));
-    }
+  }
+  for (uint32_t k = 0; k < steps; ++k) {
+    if (profile) CK(cudaEventRecord(evs[3 * k], c->st));
+    CK(launch_update(s, k, c->st));
+    if (routed) CK(launch_route(c, k));
+    if (profile) CK(cudaEventRecord(evs[3 * k + 1], c->st));
+    CK(launch_deliver(s, k, c->st));
+    if (profile) CK(cudaEventRecord(evs[3 * k + 2], c->st));
+  }
+  CK(launch_advance(s, steps, c->st));
+  if (profile) {
     CK(cudaStreamSynchronize(c->st));
     for (uint32_t k = 0; k < steps; ++k) {
       float u = 0, d = 0;
@@ -823,14 +828,8 @@ static int run_steps(snn_ctx* c, uint32_t steps) {
     for (auto& e : evs) cudaEventDestroy(e);
     c->stats.update_launches += steps;
     c->stats.deliver_launches += steps;
-    c->stats.kernel_launches += (uint64_t)steps * 2;
-    return SNN_OK;
   }
-  for (uint32_t k = 0; k < steps; ++k) {
-    CK(launch_update(s, c->st));
-    CK(launch_deliver(s, c->st));
-  }
-  if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * 2;
+  if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * (2 + (routed ? 1 : 0)) + 1;
   return SNN_OK;
 }
 
@@ -873,7 +872,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
     while (c->graph && left >= c->graph_steps) {
       CK(cudaGraphLaunch(c->graph, c->st));
       left -= c->graph_steps;
-      c->stats.kernel_launches += (uint64_t)c->graph_steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0));
+      c->stats.kernel_launches += (uint64_t)c->graph_steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0)) + 1;
     }
   }
   int rc = run_steps(c, left);

@@ -30,12 +30,9 @@ namespace snn {
 constexpr int GEN_BLOCK = 256;
 constexpr int GEN_TILE = 4096;
 constexpr int SORT_BLOCK = 256;
-constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
 constexpr int MAX_PASSES = 6;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-uint32_t sort_tile_items(uint32_t) { return SORT_TILE; }
 
 // ---------------------------------------------------------------------------
 // generation
@@ -174,11 +171,11 @@ __device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
   *(volatile unsigned long long*)p = v;
 }
 
-template <int RB>
+template <int RB, int ITEMS>
 struct SortSmem {
   static constexpr int BINS = 1 << RB;
   static constexpr int NW = SORT_BLOCK / 32;
-  uint64_t stage[SORT_TILE];
+  uint64_t stage[SORT_BLOCK * ITEMS];
   uint64_t gbase[BINS];
   uint32_t whist[NW][BINS];
   uint32_t binstart[BINS];
@@ -222,7 +219,7 @@ __device__ __forceinline__ uint64_t look_back(const BuildArgs& a, uint64_t tile,
   }
 }
 
-template <int RB>
+template <int RB, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint32_t pass,
                                                              const uint64_t* __restrict__ in,
                                                              uint64_t* __restrict__ out,
@@ -230,8 +227,9 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   constexpr int BINS = 1 << RB;
   constexpr int NW = SORT_BLOCK / 32;
   constexpr int BPT = BINS >= SORT_BLOCK ? BINS / SORT_BLOCK : 1;   // bins per thread
+  constexpr int TILE = SORT_BLOCK * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem<RB>& sm = *reinterpret_cast<SortSmem<RB>*>(smem_raw);
+  SortSmem<RB, ITEMS>& sm = *reinterpret_cast<SortSmem<RB, ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) sm.tile = atomicAdd(&a.counters[pass], 1u);
@@ -242,24 +240,24 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
 
   const uint32_t seg = upper_bound_u64(a.seg_tile0, a.g.R, tile) - 1;
   const uint64_t first_tile = a.seg_tile0[seg];
-  const uint64_t base = a.seg_start[seg] + (tile - first_tile) * SORT_TILE;
+  const uint64_t base = a.seg_start[seg] + (tile - first_tile) * TILE;
   const uint64_t seg_end = a.seg_start[seg + 1];
-  const uint32_t n = (uint32_t)min((uint64_t)SORT_TILE, seg_end - base);
+  const uint32_t n = (uint32_t)min((uint64_t)TILE, seg_end - base);
   const uint32_t shift = a.g.cbits + pass * RB;
   const uint32_t dbits = min((uint32_t)RB, a.g.key_bits - pass * RB);
   const uint64_t dmask = (1ull << dbits) - 1;
 
-  uint64_t rec[SORT_ITEMS];
-  uint32_t rnk[SORT_ITEMS];
-  const uint32_t wbase = warp * 32 * SORT_ITEMS;
+  uint64_t rec[ITEMS];
+  uint32_t rnk[ITEMS];
+  const uint32_t wbase = warp * 32 * ITEMS;
 #pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j) {
+  for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
   const uint32_t lt = (1u << lane) - 1;
 #pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j) {
+  for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -333,7 +331,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   __syncthreads();
 
 #pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j) {
+  for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     if (idx < n) {
       const uint32_t d = (uint32_t)((rec[j] >> shift) & dmask);
@@ -349,21 +347,31 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   }
 }
 
-template <int RB>
+template <int RB, int ITEMS>
 static cudaError_t sort_pass_rb(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                                 uint32_t epoch, cudaStream_t st) {
-  const size_t smem = sizeof(SortSmem<RB>);
-  cudaError_t e = cudaFuncSetAttribute(onesweep_pass<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(SortSmem<RB, ITEMS>);
+  cudaError_t e = cudaFuncSetAttribute(onesweep_pass<RB, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  onesweep_pass<RB><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, smem, st>>>(a, pass, in, out, epoch);
+  onesweep_pass<RB, ITEMS><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, smem, st>>>(a, pass, in, out, epoch);
   return cudaGetLastError();
 }
+
+bool sort_config_supported(uint32_t radix_bits, uint32_t items) {
+  return (radix_bits == 8 || radix_bits == 9) && (items == 8 || items == 12 || items == 16);
+}
+
+uint32_t sort_tile_items(uint32_t items) { return SORT_BLOCK * items; }
 
 cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                              uint32_t epoch, cudaStream_t st) {
   if (a.n_sort_tiles == 0) return cudaSuccess;
-  if (a.radix_bits == 8) return sort_pass_rb<8>(a, pass, in, out, epoch, st);
-  if (a.radix_bits == 9) return sort_pass_rb<9>(a, pass, in, out, epoch, st);
+#define SNN_SORT_CASE(RB_, IT_) \
+  if (a.radix_bits == RB_ && a.sort_items == IT_) return sort_pass_rb<RB_, IT_>(a, pass, in, out, epoch, st);
+  SNN_SORT_CASE(8, 8) SNN_SORT_CASE(8, 12) SNN_SORT_CASE(8, 16)
+  SNN_SORT_CASE(9, 8) SNN_SORT_CASE(9, 12) SNN_SORT_CASE(9, 16)
+#undef SNN_SORT_CASE
   return cudaErrorInvalidValue;
 }
 
@@ -606,8 +614,9 @@ __global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
       cur = seg;
     }
     __syncthreads();
-    const uint64_t base = a.seg_start[seg] + (tile - a.seg_tile0[seg]) * SORT_TILE;
-    const uint64_t end = min(base + SORT_TILE, a.seg_start[seg + 1]);
+    const uint64_t tile_n = (uint64_t)SORT_BLOCK * a.sort_items;
+    const uint64_t base = a.seg_start[seg] + (tile - a.seg_tile0[seg]) * tile_n;
+    const uint64_t end = min(base + tile_n, a.seg_start[seg + 1]);
     for (uint64_t i = base + threadIdx.x; i < end; i += 256) {
       const uint64_t kk = a.rec_a[i] >> a.g.cbits;
 #pragma unroll

@@ -461,8 +461,8 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
 
 // ---- routing: spikes -> delivery work items (global rows) ----
 namespace {
-__global__ void route_kernel(RouteArgs r) {
-  const uint32_t n = *r.step;
+__global__ void route_kernel(RouteArgs r, uint32_t k_step) {
+  const uint32_t n = *r.step + k_step;
   const uint32_t nspk = r.n_spk[n & 1];
   const uint32_t* spk = r.spk + (uint64_t)(n & 1) * r.N;
   if (blockIdx.x == 0 && threadIdx.x == 0) r.n_work[(n + 1) & 1] = 0;
@@ -547,9 +547,9 @@ int setup_routing(snn_ctx* c) {
   return SNN_OK;
 }
 
-cudaError_t launch_route(snn_ctx* c) {
+cudaError_t launch_route(snn_ctx* c, uint32_t k_step) {
   MapsState& m = ctx_maps(c);
-  route_kernel<<<(unsigned)std::max(1, ctx_num_sms(c) * 2), 256, 0, ctx_stream(c)>>>(m.route);
+  route_kernel<<<(unsigned)std::max(1, ctx_num_sms(c) * 2), 256, 0, ctx_stream(c)>>>(m.route, k_step);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ uint32_t ctx_N(snn_ctx* c);
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs,
                const uint64_t* d_cbase);
 int setup_routing(snn_ctx* c);
-cudaError_t launch_route(snn_ctx* c);
+cudaError_t launch_route(snn_ctx* c, uint32_t k_step);
 uint32_t route_kernels_per_step(snn_ctx* c);
 int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp);
 int rank_row_scales(snn_ctx* c, uint32_t rank, std::vector<float>* scales);

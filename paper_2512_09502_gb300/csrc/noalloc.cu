@@ -30,7 +30,7 @@ namespace {
 constexpr uint64_t kMaxSynapses = SNN_NOALLOC_MAX_SYNAPSES;
 constexpr uint32_t kBins = 256;            // radix 8 (the only sort width built)
 constexpr uint32_t kMaxPasses = 6;
-constexpr uint64_t kTile = 4096;           // sort tile of build.cu (SORT_BLOCK x SORT_ITEMS)
+constexpr uint64_t kTile = 4096;           // sort tile: 256 threads x 16 records
 constexpr uint64_t kMaxTiles = (kMaxSynapses + kTile - 1) / kTile;
 
 struct Scratch {
@@ -214,6 +214,7 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   a.tgt = dev_tgt; a.w = dev_w; a.d = dev_d; a.w_format = 0;
   a.dense = dev_row_ptr; a.row_scale_src = nullptr;
   a.fuse_hist = 1;
+  a.sort_items = 16;
 
   NA_CK(launch_generate(a, st));
   NA_CK(launch_bin_scan(a, st));

@@ -14,9 +14,10 @@
 //
 // One step = update_kernel (reads and clears ring slot n, integrates, appends spikes
 // to the per-step delivery list) then deliver_kernel (walks the rows of every listed
-// spike and red.add's the weights into slots n + d); the last deliver CTA to finish
-// advances the device-side step counter, so the step needs no host involvement and
-// is captured as a CUDA graph.
+// spike and red.add's the weights into slots n + d).  The step needs no host involvement
+// and is captured as a CUDA graph.  The step index of a launch is *step + k, with k baked
+// into the launch (or graph node); one advance kernel after a batch of steps adds the
+// batch length, so no per-step completion handshake is needed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -30,13 +31,23 @@ constexpr int DEL_BLOCK = 256;
 constexpr int DEL_ILP = 4;        // events per thread per iteration
 constexpr uint32_t MAX_SMEM_DRIVES = 16;
 
-__global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
+// #{i < len : thr[i] <= w}; thresholds are ascending
+__device__ __forceinline__ uint32_t table_count(const uint32_t* thr, uint32_t len, uint32_t w) {
+  if (len <= 32) {           // short tables (Poisson counts): independent compares
+    uint32_t c = 0;
+    for (uint32_t i = 0; i < len; ++i) c += thr[i] <= w ? 1u : 0u;
+    return c;
+  }
+  return upper_bound_u32(thr, len, w);
+}
+
+__global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k_step) {
   __shared__ uint32_t s_tbl[256];
   __shared__ DevPop s_pop[64];
   __shared__ DevDrive s_dr[MAX_SMEM_DRIVES];
   const int tid = threadIdx.x;
   const uint32_t lane = tid & 31;
-  const uint32_t n = *a.step;
+  const uint32_t n = *a.step + k_step;
   for (uint32_t i = tid; i < a.poisson_tbl_len && i < 256; i += UPD_BLOCK) s_tbl[i] = a.poisson_tbl[i];
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
   for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
@@ -48,7 +59,9 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
   const uint64_t stride = (uint64_t)gridDim.x * UPD_BLOCK * UPD_ILP;
   for (uint64_t base = (uint64_t)blockIdx.x * UPD_BLOCK * UPD_ILP; base < a.N; base += stride) {
     float V[UPD_ILP], Iex[UPD_ILP], Iin[UPD_ILP], in_ex[UPD_ILP], in_in[UPD_ILP];
-    uint32_t refr[UPD_ILP], pi[UPD_ILP];
+    uint32_t refr[UPD_ILP], pi[UPD_ILP], gid[UPD_ILP];
+    bool spike[UPD_ILP];
+    // phase 1: every load of the four neurons
 #pragma unroll
     for (int k = 0; k < UPD_ILP; ++k) {
       const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
@@ -57,16 +70,16 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
         refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
         in_ex[k] = rex[i];
         in_in[k] = a.n_rec == 2 ? rin[i] : 0.f;
+        gid[k] = a.R == 1 ? (uint32_t)i : a.gid_of[i];
       }
     }
+    // phase 2: integrate (independent chains, interleaved by the compiler)
 #pragma unroll
     for (int k = 0; k < UPD_ILP; ++k) {
       const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
-      bool spike = false;
-      uint32_t gid = 0;
+      spike[k] = false;
       if (i < a.N) {
         const DevPop P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
-        gid = a.R == 1 ? (uint32_t)i : a.gid_of[i];
         float v = V[k], ie = Iex[k], ii = Iin[k];
         uint32_t rf = refr[k];
         if (rf == 0) v = P.P22 * v + P.P21ex * ie + P.P21in * ii + P.P20 * P.Ie;
@@ -75,40 +88,55 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a) {
         ii = P.P11in * ii + in_in[k];
         for (uint32_t q = 0; q < a.ndrives; ++q) {
           const DevDrive dr = q < MAX_SMEM_DRIVES ? s_dr[q] : a.drives[q];
-          if (gid - dr.first < dr.n) {
-            const uint4 b = philox_stream((uint64_t)gid | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
-            const uint32_t cnt = upper_bound_u32(s_tbl + dr.tbl_off, dr.tbl_len, b.x);
+          if (gid[k] - dr.first < dr.n) {
+            const uint4 b = philox_stream((uint64_t)gid[k] | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
+            const uint32_t cnt = table_count(s_tbl + dr.tbl_off, dr.tbl_len, b.x);
             if (dr.weight >= 0.f || a.n_rec == 1) ie += (float)cnt * dr.weight; else ii += (float)cnt * dr.weight;
           }
         }
         if (v >= P.Vth) {
           v = P.Vreset;
           rf = P.ref_steps;
-          spike = true;
+          spike[k] = true;
         }
-        a.V[i] = v;
-        a.Iex[i] = ie;
-        a.Iin[i] = ii;
-        a.refr[i] = (uint16_t)rf;
+        V[k] = v; Iex[k] = ie; Iin[k] = ii; refr[k] = rf;
+      }
+    }
+    // phase 3: stores, ring slot cleared, spikes appended
+#pragma unroll
+    for (int k = 0; k < UPD_ILP; ++k) {
+      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
+      if (i < a.N) {
+        a.V[i] = V[k];
+        a.Iex[i] = Iex[k];
+        a.Iin[i] = Iin[k];
+        a.refr[i] = (uint16_t)refr[k];
         rex[i] = 0.f;
         if (a.n_rec == 2) rin[i] = 0.f;
       }
+    }
+#pragma unroll
+    for (int k = 0; k < UPD_ILP; ++k) {
       // warp-aggregated append of the step's spiking positions (on one rank these are
       // directly the rows to deliver; with several ranks the router expands them)
-      const uint32_t mask = __ballot_sync(0xffffffffu, spike);
+      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
+      const uint32_t mask = __ballot_sync(0xffffffffu, spike[k]);
       if (mask) {
         const int leader = __ffs(mask) - 1;
         uint32_t sbase = 0;
-        if ((int)lane == leader) sbase = atomicAdd(&a.n_spk[n & 1], __popc(mask));
+        if ((int)lane == leader) {
+          sbase = atomicAdd(&a.n_spk[n & 1], __popc(mask));
+          atomicAdd(a.n_spikes_total, (unsigned long long)__popc(mask));
+        }
         sbase = __shfl_sync(0xffffffffu, sbase, leader);
         const uint32_t off = __popc(mask & ((1u << lane) - 1));
-        if (spike) {
+        if (spike[k]) {
           a.spk[(uint64_t)(n & 1) * a.N + sbase + off] = (uint32_t)i;
           unsigned long long lb = 0;
           if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
           lb = __shfl_sync(mask, lb, leader);
           const unsigned long long ls = lb + off;
-          if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid);
+          if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid[k]);
         }
       }
     }
@@ -163,8 +191,9 @@ __device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e, uin
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT* __restrict__ w) {
-  const uint32_t n = *a.step;
+__global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT* __restrict__ w,
+                                                            uint32_t k_step) {
+  const uint32_t n = *a.step + k_step;
   const uint32_t nitems = a.n_work[n & 1];
   const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
   const uint32_t slices = a.slices;
@@ -211,22 +240,9 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
     }
     if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);
   }
-  // the last CTA to finish advances the step counter
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t ticket = atomicAdd(a.done, 1u);
-    s_last = ticket == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x == 0) {
-    *a.n_spikes_total += nitems;
-    *a.done = 0;
-    __threadfence();
-    *a.step = n + 1;
-  }
 }
+
+__global__ void advance_step_kernel(uint32_t* step, uint32_t by) { *step += by; }
 
 __global__ void init_state_kernel(SimArgs a, const float* v0) {
   const uint64_t total = (uint64_t)a.N;
@@ -239,21 +255,26 @@ __global__ void init_state_kernel(SimArgs a, const float* v0) {
   }
 }
 
-cudaError_t launch_update(const SimArgs& a, cudaStream_t st) {
+cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
   const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_ILP - 1) / (UPD_BLOCK * UPD_ILP);
   const unsigned grid = (unsigned)(need < a.update_grid ? need : a.update_grid);
-  update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a);
+  update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a, k_step);
   return cudaGetLastError();
 }
 
-cudaError_t launch_deliver(const SimArgs& a, cudaStream_t st) {
+cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
   const unsigned grid = (unsigned)a.deliver_grid;
   if (a.w_format == 0)
-    deliver_kernel<float><<<grid, DEL_BLOCK, 0, st>>>(a, (const float*)a.w);
+    deliver_kernel<float><<<grid, DEL_BLOCK, 0, st>>>(a, (const float*)a.w, k_step);
   else if (a.w_format == 1)
-    deliver_kernel<__nv_bfloat16><<<grid, DEL_BLOCK, 0, st>>>(a, (const __nv_bfloat16*)a.w);
+    deliver_kernel<__nv_bfloat16><<<grid, DEL_BLOCK, 0, st>>>(a, (const __nv_bfloat16*)a.w, k_step);
   else
-    deliver_kernel<__half><<<grid, DEL_BLOCK, 0, st>>>(a, (const __half*)a.w);
+    deliver_kernel<__half><<<grid, DEL_BLOCK, 0, st>>>(a, (const __half*)a.w, k_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st) {
+  advance_step_kernel<<<1, 1, 0, st>>>(a.step, by);
   return cudaGetLastError();
 }
 

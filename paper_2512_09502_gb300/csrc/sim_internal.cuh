@@ -14,13 +14,12 @@ struct SimArgs {
   const uint32_t* poisson_tbl; uint32_t poisson_tbl_len;
   float* ring; uint32_t ring_mask;            // [D][n_rec][N]
   uint32_t n_rec;                             // 2 receptors, or 1 when tau_ex == tau_in
-  uint32_t* step;                             // device step counter
+  uint32_t* step;                             // device step counter (first step of a batch)
   uint32_t* n_spk; uint32_t* spk;             // [2] counts, [2][N] spiking positions
   uint32_t* n_work; uint32_t* work;           // [2] counts, [2][stride] rows to deliver
   uint64_t work_stride;
   unsigned long long* n_logged; uint2* log; unsigned long long log_cap;
   unsigned long long* n_events; unsigned long long* n_spikes_total;
-  uint32_t* done;
   const uint64_t* rows;                       // row starts (absolute); one rank: gid rows
   const uint64_t* rows_off;                   // [R+1] first row of each rank (R > 1)
   const uint32_t* rank_off;                   // [R+1] first neuron position of each rank
@@ -30,8 +29,9 @@ struct SimArgs {
   uint32_t deliver_grid, update_grid;
 };
 
-cudaError_t launch_update(const SimArgs& a, cudaStream_t st);
-cudaError_t launch_deliver(const SimArgs& a, cudaStream_t st);
+cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st);
+cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st);
+cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st);
 cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st);
 
 }  // namespace snn

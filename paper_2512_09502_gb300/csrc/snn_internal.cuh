@@ -162,6 +162,7 @@ struct BuildArgs {
   const float* row_scale_src; // per source gid (fp16 format) or null
   int num_sms;
   uint32_t fuse_hist;         // generation accumulates the sort histograms itself
+  uint32_t sort_items;        // records per thread of a sort tile (tile = 256 x items)
 };
 
 // counted generation (fixed total over several ranks; pairwise Bernoulli): the
@@ -198,6 +199,7 @@ cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                              uint32_t epoch, cudaStream_t st);
 cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E, cudaStream_t st);
-uint32_t sort_tile_items(uint32_t radix_bits);
+uint32_t sort_tile_items(uint32_t items);
+bool sort_config_supported(uint32_t radix_bits, uint32_t items);
 
 }  // namespace snn
