@@ -35,7 +35,11 @@ if ROOT not in sys.path:
 METRIC = "synapses built/s + synaptic events/s (1 GB300, % HBM peak), bf16 vs fp32 weights"
 UNIT = "(synapses + events)/s"
 # algorithmic bytes per unit of the measured kernels
-BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize": 17.0, "generate": 8.0}
+BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize": 17.0, "generate": 8.0,
+         "update": 38.0}
+
+
+WORKLOADS = ("balanced_500k", "balanced_5k", "multi_area", "multi_area_r128")
 
 
 def workload(name: str, scale: float):
@@ -44,6 +48,10 @@ def workload(name: str, scale: float):
         return wl.balanced_scaled(scale)
     if name == "balanced_5k":
         return wl.balanced_small()
+    if name == "multi_area":            # 32 areas, ~1M neurons, 2,328 blocks, one rank
+        return wl.multi_area(scale=scale)
+    if name == "multi_area_r128":       # the same network over 128 logical ranks
+        return wl.multi_area(scale=scale, n_ranks=128)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -192,9 +200,17 @@ def run_ours(args):
     alloc = _lib.TorchAllocator(local)
     stream = torch.cuda.current_stream()
 
+    # launch parameters: tuned once on this workload (outside every timed region)
+    from paper_2512_09502_gb300 import autotune
+    tuned = autotune.load()
+    if args.autotune and (tuned is None or tuned.get("network") != net.name):
+        tuned = autotune.tune(net, allocator=alloc, stream=stream.cuda_stream, device=local,
+                              sim_steps=min(args.sim_steps, 1000))
+    knobs = {k: int(tuned[k]) for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm")} if tuned else {}
+
     def one(fmt, sim_steps, profile=False):
         ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
-                                 device=local, use_graph=True, profile_kernels=profile)
+                                 device=local, use_graph=True, profile_kernels=profile, **knobs)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ctx.calibrate()
@@ -265,7 +281,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t = time.perf_counter()
         ctx = _lib.build_network(net, weight_format="f32", allocator=alloc, stream=stream.cuda_stream,
-                                 device=local, use_graph=True)
+                                 device=local, use_graph=True, **knobs)
         ctx.calibrate()
         ctx.simulate(args.sim_steps)
         st = ctx.stats()
@@ -280,29 +296,32 @@ def run_ours(args):
     _, prof = one("f32", min(args.sim_steps, 2000), profile=True)
     peak, peak_kind = peaks()
     E = prof["n_synapses"]
-    per_pass_ms = prof["t_sort_pass_ms"] / max(prof["sort_passes"], 1)
-    deliver_ms = prof["t_deliver_ms"] / max(prof["deliver_launches"], 1)
-    events_per_launch = prof["n_events"] / max(prof["deliver_launches"], 1)
     step_ms = ms / args.steps
-    share = {"sort_pass": prof["t_sort_pass_ms"] / step_ms,
-             "deliver": deliver_ms * args.sim_steps / step_ms}
-    dominant = max(share, key=share.get)
-    if dominant == "sort_pass":
-        alg = E * BYTES["sort_pass"]
-        ach = alg / (per_pass_ms / 1000.0) / 1e9
-        kern, units_launch = "onesweep_pass", E
-    else:
-        alg = events_per_launch * BYTES["deliver_f32"]
-        ach = alg / (deliver_ms / 1000.0) / 1e9
-        kern, units_launch = "deliver_kernel", events_per_launch
-    roof = {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic_of(kern, units_launch),
-            "algorithmic_bytes_per_launch": alg,
-            "shares_of_step": share,
-            "sort_pass": {"ms_per_launch": per_pass_ms, "GBps": E * 16 / (per_pass_ms / 1000) / 1e9},
-            "deliver": {"ms_per_launch": deliver_ms, "events_per_launch": events_per_launch,
-                        "GBps": events_per_launch * 13 / (deliver_ms / 1000) / 1e9 if deliver_ms else None},
-            "update": {"ms_per_launch": prof["t_update_ms"] / max(prof["update_launches"], 1)}}
+    dl = max(prof["deliver_launches"], 1)
+    ev_launch = prof["n_events"] / dl
+    kern = {
+        "gen_kernel": dict(ms=prof["t_generate_ms"], launches=1, units=E, bpu=BYTES["generate"], bound="alu"),
+        "onesweep_pass": dict(ms=prof["t_sort_pass_ms"] / max(prof["sort_passes"], 1), launches=prof["sort_passes"],
+                              units=E, bpu=BYTES["sort_pass"], bound="hbm"),
+        "finalize_kernel": dict(ms=prof["t_finalize_ms"], launches=1, units=E, bpu=BYTES["finalize"], bound="hbm"),
+        "update_kernel": dict(ms=prof["t_update_ms"] / max(prof["update_launches"], 1), launches=args.sim_steps,
+                              units=net.n_neurons, bpu=BYTES["update"], bound="hbm"),
+        "deliver_kernel": dict(ms=prof["t_deliver_ms"] / dl, launches=args.sim_steps, units=ev_launch,
+                               bpu=BYTES["deliver_f32"], bound="hbm"),
+    }
+    table = {}
+    for k, v in kern.items():
+        gbps = v["units"] * v["bpu"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None
+        table[k] = {"ms_per_launch": v["ms"], "launches_per_step": v["launches"],
+                    "share_of_step": v["ms"] * v["launches"] / step_ms, "algorithmic_GBps": gbps,
+                    "frac_of_hbm": gbps / peak if gbps else None}
+    dom = max((k for k in kern if kern[k]["bound"] == "hbm"), key=lambda k: table[k]["share_of_step"])
+    d = kern[dom]
+    alg = d["units"] * d["bpu"]
+    ach = alg / (d["ms"] / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "traffic": traffic_of(dom, d["units"]), "algorithmic_bytes_per_launch": alg,
+            "kernels": table}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -317,7 +336,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "neurons": net.n_neurons, "synapses": s0["n_synapses"],
                        "sim_steps": args.sim_steps, "dt_ms": net.dt, "drive_hz": net.drives[0].rate_hz if net.drives else 0.0,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "working set (50.6 GB layout) far larger than L2"},
+                       "n_ranks": net.n_ranks, "l2": "working set (connection layout) far larger than L2"},
             "components": {"synapses_built_per_s": syn_per_s, "synaptic_events_per_s": ev_per_s,
                            "construct_ms": s0["t_calibrate_ms"], "simulate_ms": s0["t_simulate_ms"],
                            "generate_ms": s0["t_generate_ms"], "sort_ms": s0["t_sort_ms"],
@@ -325,6 +344,7 @@ def run_ours(args):
                            "rate_hz": s0["n_spikes"] / net.n_neurons / (args.sim_steps * net.dt / 1000.0),
                            "peak_device_GB": s0["peak_device_bytes"] / 1e9},
             "bf16": bf,
+            "tuned": knobs,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -344,7 +364,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="balanced_500k")
+    ap.add_argument("--workload", default="balanced_500k", choices=WORKLOADS)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--sim-steps", type=int, default=10_000)
     ap.add_argument("--ref-neurons", type=int, default=1000)

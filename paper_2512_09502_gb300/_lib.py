@@ -164,6 +164,12 @@ class Context:
                  stream: Optional[int] = None, profile_kernels: bool = False, sort_items: int = 0,
                  deliver_ctas_per_sm: int = 0):
         self.lib = load()
+        if not (radix_bits and sort_items and deliver_ctas_per_sm):
+            from . import autotune        # tuned launch parameters, when a cache exists
+            tuned = autotune.load() or {}
+            radix_bits = radix_bits or int(tuned.get("radix_bits", 0))
+            sort_items = sort_items or int(tuned.get("sort_items", 0))
+            deliver_ctas_per_sm = deliver_ctas_per_sm or int(tuned.get("deliver_ctas_per_sm", 0))
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
                          1 if profile_kernels else 0, sort_items, deliver_ctas_per_sm)

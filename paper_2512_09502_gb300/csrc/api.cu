@@ -287,7 +287,7 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
   if (cudaSetDevice(config->device) != cudaSuccess) return SNN_ECUDA;
   snn_ctx* c = new snn_ctx();
   c->cfg = *config;
-  if (c->cfg.radix_bits == 0) c->cfg.radix_bits = 8;
+  if (c->cfg.radix_bits == 0) c->cfg.radix_bits = 9;
   if (c->cfg.sort_items == 0) c->cfg.sort_items = 16;
   if (c->cfg.deliver_ctas_per_sm == 0) c->cfg.deliver_ctas_per_sm = 8;
   if (alloc) c->alloc = *alloc;
@@ -453,10 +453,25 @@ int snn_calibrate(snn_ctx* c) {
   g.cbits = std::max(1u, bits_for(ctot ? ctot - 1 : 0));
   g.magic_R = magic_for(R);
   if (g.key_bits + g.cbits > 64) return fail(c, SNN_EINVAL, "network too large for 64-bit sort records");
+  // pass plan: as few passes as digits of at most radix_bits allow, 8-bit digits
+  // wherever possible (a 9-bit pass costs more than an 8-bit one)
   const uint32_t RB = (uint32_t)c->cfg.radix_bits;
-  const uint32_t BINS = 1u << RB;
+  const uint32_t BINS = kHistStride;
   const uint32_t passes = (g.key_bits + RB - 1) / RB;
   if (passes > 6) return fail(c, SNN_EINVAL, "sort key too wide");
+  uint8_t pass_bits[8] = {0}, pass_shift[8] = {0};
+  {
+    const int nine = std::max(0, (int)g.key_bits - 8 * (int)passes);
+    uint32_t left = g.key_bits, sh = 0;
+    for (uint32_t p = 0; p < passes; ++p) {
+      uint32_t w = (p >= passes - (uint32_t)nine) ? 9u : 8u;
+      w = std::min(w, left);
+      pass_bits[p] = (uint8_t)w;
+      pass_shift[p] = (uint8_t)sh;
+      sh += w;
+      left -= w;
+    }
+  }
 
   // ---- counted projections: fixed total over several ranks, pairwise Bernoulli ----
   DevProj* d_projs;
@@ -610,6 +625,7 @@ int snn_calibrate(snn_ctx* c) {
   a.dense_off = c->d_dense_off;
   a.fuse_hist = counted ? 0u : 1u;
   a.sort_items = (uint32_t)c->cfg.sort_items;
+  for (int p = 0; p < 8; ++p) { a.pass_bits[p] = pass_bits[p]; a.pass_shift[p] = pass_shift[p]; }
 
   CK(launch_generate(a, c->st));
   c->stats.kernel_launches += tiles ? 1 : 0;

@@ -37,9 +37,8 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // ---------------------------------------------------------------------------
 // generation
 // ---------------------------------------------------------------------------
-template <int RB>
 __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
-  constexpr int BINS = 1 << RB;
+  constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
   __shared__ uint32_t s_tbl[256];
   __shared__ DevBlock s_blk;
@@ -112,7 +111,8 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       if (a.fuse_hist) {
 #pragma unroll
         for (int p = 0; p < MAX_PASSES; ++p)
-          if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+          if (p < (int)passes)
+            atomicAdd(&s_hist[p][(kk >> a.pass_shift[p]) & ((1u << a.pass_bits[p]) - 1)], 1u);
       }
     }
   }
@@ -128,32 +128,29 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
 cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st) {
   if (a.n_gen_tiles == 0) return cudaSuccess;
   const uint64_t grid = std::min<uint64_t>(a.n_gen_tiles, (uint64_t)a.num_sms * 8);
-  if (a.radix_bits == 8) gen_kernel<8><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
-  else if (a.radix_bits == 9) gen_kernel<9><<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
-  else return cudaErrorInvalidValue;
+  gen_kernel<<<(unsigned)grid, GEN_BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // histogram scan -> bin bases (absolute positions)
 // ---------------------------------------------------------------------------
-__global__ void bin_scan_kernel(const uint64_t* hist, uint64_t* base, const uint64_t* seg_start,
-                                uint32_t R, uint32_t passes, uint32_t bins) {
+__global__ void bin_scan_kernel(BuildArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= R * passes) return;
-  const uint32_t r = i / passes;
-  uint64_t acc = seg_start[r];
+  if (i >= a.g.R * a.passes) return;
+  const uint32_t r = i / a.passes, p = i - r * a.passes;
+  const uint32_t bins = 1u << a.pass_bits[p];
+  uint64_t acc = a.seg_start[r];
   for (uint32_t b = 0; b < bins; ++b) {
-    base[(uint64_t)i * bins + b] = acc;
-    acc += hist[(uint64_t)i * bins + b];
+    a.bin_base[(uint64_t)i * kHistStride + b] = acc;
+    acc += a.hist[(uint64_t)i * kHistStride + b];
   }
 }
 
 cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st) {
   const uint32_t n = a.g.R * a.passes;
   if (n == 0) return cudaSuccess;
-  bin_scan_kernel<<<(n + 127) / 128, 128, 0, st>>>(a.hist, a.bin_base, a.seg_start, a.g.R, a.passes,
-                                                  1u << a.radix_bits);
+  bin_scan_kernel<<<(n + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -243,9 +240,8 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   const uint64_t base = a.seg_start[seg] + (tile - first_tile) * TILE;
   const uint64_t seg_end = a.seg_start[seg + 1];
   const uint32_t n = (uint32_t)min((uint64_t)TILE, seg_end - base);
-  const uint32_t shift = a.g.cbits + pass * RB;
-  const uint32_t dbits = min((uint32_t)RB, a.g.key_bits - pass * RB);
-  const uint64_t dmask = (1ull << dbits) - 1;
+  const uint32_t shift = a.g.cbits + a.pass_shift[pass];
+  const uint64_t dmask = (1ull << a.pass_bits[pass]) - 1;
 
   uint64_t rec[ITEMS];
   uint32_t rnk[ITEMS];
@@ -307,7 +303,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
       excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
       st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
     }
-    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * BINS + b] + excl;
+    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * kHistStride + b] + excl;
   }
 
   // tile-local exclusive scan of the bin counts (thread-contiguous bins)
@@ -367,8 +363,9 @@ uint32_t sort_tile_items(uint32_t items) { return SORT_BLOCK * items; }
 cudaError_t launch_sort_pass(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                              uint32_t epoch, cudaStream_t st) {
   if (a.n_sort_tiles == 0) return cudaSuccess;
+  const uint32_t rb = a.pass_bits[pass] <= 8 ? 8u : 9u;   // kernel width for this pass's digit
 #define SNN_SORT_CASE(RB_, IT_) \
-  if (a.radix_bits == RB_ && a.sort_items == IT_) return sort_pass_rb<RB_, IT_>(a, pass, in, out, epoch, st);
+  if (rb == RB_ && a.sort_items == IT_) return sort_pass_rb<RB_, IT_>(a, pass, in, out, epoch, st);
   SNN_SORT_CASE(8, 8) SNN_SORT_CASE(8, 12) SNN_SORT_CASE(8, 16)
   SNN_SORT_CASE(9, 8) SNN_SORT_CASE(9, 12) SNN_SORT_CASE(9, 16)
 #undef SNN_SORT_CASE
@@ -592,9 +589,8 @@ cudaError_t launch_counted_place(const CountedArgs& c, const BuildArgs& a, cudaS
 }
 
 // per-segment digit histograms of all records (when generation could not fuse them)
-template <int RB>
 __global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
-  constexpr int BINS = 1 << RB;
+  constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
   const uint32_t passes = a.passes;
   for (int i = threadIdx.x; i < MAX_PASSES * BINS; i += 256) (&s_hist[0][0])[i] = 0;
@@ -621,7 +617,7 @@ __global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
       const uint64_t kk = a.rec_a[i] >> a.g.cbits;
 #pragma unroll
       for (int p = 0; p < MAX_PASSES; ++p)
-        if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> (p * RB)) & (BINS - 1)], 1u);
+        if (p < (int)passes) atomicAdd(&s_hist[p][(kk >> a.pass_shift[p]) & ((1u << a.pass_bits[p]) - 1)], 1u);
     }
   }
   __syncthreads();
@@ -635,9 +631,7 @@ __global__ void __launch_bounds__(256) hist_kernel(BuildArgs a) {
 cudaError_t launch_histogram(const BuildArgs& a, cudaStream_t st) {
   if (a.n_sort_tiles == 0 || a.passes == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<uint64_t>(a.n_sort_tiles, (uint64_t)a.num_sms * 8);
-  if (a.radix_bits == 8) hist_kernel<8><<<grid, 256, 0, st>>>(a);
-  else if (a.radix_bits == 9) hist_kernel<9><<<grid, 256, 0, st>>>(a);
-  else return cudaErrorInvalidValue;
+  hist_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -37,8 +37,8 @@ struct Scratch {
   uint64_t rec_a[kMaxSynapses];
   uint64_t rec_b[kMaxSynapses];
   uint64_t status[kMaxTiles * kBins];
-  uint64_t hist[kMaxPasses * kBins];
-  uint64_t bin_base[kMaxPasses * kBins];
+  uint64_t hist[kMaxPasses * kHistStride];
+  uint64_t bin_base[kMaxPasses * kHistStride];
   uint64_t seg_start[2];
   uint64_t seg_tile0[2];
   uint64_t cbase[1];
@@ -166,6 +166,12 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   g.magic_R = magic_for(1);
   const uint32_t passes = (g.key_bits + 7) / 8;
   if (passes > kMaxPasses || g.key_bits + g.cbits > 64) NA_FAIL(SNN_EINVAL, "network too large");
+  uint8_t pass_bits[8] = {0}, pass_shift[8] = {0};
+  for (uint32_t p = 0, sh = 0; p < passes; ++p) {     // 8-bit digits, the last one narrower
+    pass_bits[p] = (uint8_t)std::min(8u, g.key_bits - sh);
+    pass_shift[p] = (uint8_t)sh;
+    sh += pass_bits[p];
+  }
 
   DevProj P{};
   P.src_first = src_first; P.n_src = n_src; P.src_stride = 1;
@@ -215,6 +221,7 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   a.dense = dev_row_ptr; a.row_scale_src = nullptr;
   a.fuse_hist = 1;
   a.sort_items = 16;
+  for (int p = 0; p < 8; ++p) { a.pass_bits[p] = pass_bits[p]; a.pass_shift[p] = pass_shift[p]; }
 
   NA_CK(launch_generate(a, st));
   NA_CK(launch_bin_scan(a, st));

@@ -163,7 +163,11 @@ struct BuildArgs {
   int num_sms;
   uint32_t fuse_hist;         // generation accumulates the sort histograms itself
   uint32_t sort_items;        // records per thread of a sort tile (tile = 256 x items)
+  // pass plan: digit p is (key >> pass_shift[p]) & ((1 << pass_bits[p]) - 1); histogram
+  // and bin arrays use kHistStride bins per pass
+  uint8_t pass_shift[8], pass_bits[8];
 };
+constexpr uint32_t kHistStride = 512;
 
 // counted generation (fixed total over several ranks; pairwise Bernoulli): the
 // records of such a projection land in (rank, projection) blocks whose sizes are
