@@ -149,6 +149,18 @@ def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000):
                                    f"then simulated {sim_steps} steps ({events} events)")
 
 
+def aggregate(units: float, ms: float, dist=None, device: str = "cpu"):
+    """Whole-job aggregate over ranks: units summed, time = the slowest rank's."""
+    if dist is None:
+        return units, ms
+    import torch
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -226,19 +238,6 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
 
     def timed(fmt):
         for _ in range(args.warmup):
@@ -254,9 +253,9 @@ def run_ours(args):
         t1.record(stream)
         barrier()
         clocks = clk.stop()
-        ms = max_over_ranks(t0.elapsed_time(t1))
-        units = sum(s["n_synapses"] + s["n_events"] for s in stats)
-        return ms, sum_over_ranks(units), stats, clocks
+        units, ms = aggregate(sum(s["n_synapses"] + s["n_events"] for s in stats), t0.elapsed_time(t1),
+                              dist, "cuda")
+        return ms, units, stats, clocks
 
     ms, units, stats, clocks = timed("f32")
     value = units / (ms / 1000.0)
@@ -289,8 +288,7 @@ def run_ours(args):
         e2e_ms += 1000 * (time.perf_counter() - t)
         e2e_units += st["n_synapses"] + st["n_events"]
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
-    e2e_ms = max_over_ranks(e2e_ms)
-    e2e_units = sum_over_ranks(e2e_units)
+    e2e_units, e2e_ms = aggregate(e2e_units, e2e_ms, dist, "cuda")
 
     # per-kernel CUDA-event times for the roofline (outside the timed region)
     _, prof = one("f32", min(args.sim_steps, 2000), profile=True)

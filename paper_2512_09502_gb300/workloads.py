@@ -180,9 +180,14 @@ def balanced_scaled(scale: float = 1.0, **kw) -> Network:
                     name=f"balanced_{n_e + n_i}", **kw)
 
 
+MULTI_AREA_G = 10.0            # J_I = -10 J_E: E in-degree ~3,500 vs I ~500 per target
+MULTI_AREA_DRIVE_HZ = 23000.0
+
+
 def multi_area(seed: int = 1234, n_areas: int = 32, area_mean: float = 31250.0,
                n_ranks: int = 1, scale: float = 1.0, per_pair_indegree: bool = False,
-               inter_mean_indegree: float = 1500.0) -> Network:
+               inter_mean_indegree: float = 1500.0, g: float = MULTI_AREA_G,
+               drive_rate_hz: float = MULTI_AREA_DRIVE_HZ) -> Network:
     """Synthetic multi-area network: ``n_areas`` areas x 8 populations (E then I, 4
     layers each), area sizes lognormal (sigma 0.3, mean preserved), intra-area 8x8
     fixed-total projections with p ~ U(0.01, 0.15), 30% of ordered area pairs
@@ -190,7 +195,10 @@ def multi_area(seed: int = 1234, n_areas: int = 32, area_mean: float = 31250.0,
     with a fixed in-degree.  By default ``inter_mean_indegree`` is each neuron's total
     inter-area in-degree, split over its connected source areas; with
     ``per_pair_indegree`` it is the mean per connected pair.  Inter-area delays are
-    distance / 3.5 m/s with distance ~ U(5, 50) mm and a 10% sd."""
+    distance / 3.5 m/s with distance ~ U(5, 50) mm and a 10% sd.  With the balanced
+    network's g = 5 the E in-degree (~3,500 per target) exceeds g times the I in-degree
+    (~500), so the network is either silent or saturated; g = 10 gives it an
+    inhibition-dominated (balanced) regime like the paper's models."""
     rng = np.random.default_rng(seed)
     z = rng.standard_normal(n_areas)
     sizes = np.rint(area_mean * scale * np.exp(0.3 * z - 0.045)).astype(np.int64)
@@ -212,7 +220,7 @@ def multi_area(seed: int = 1234, n_areas: int = 32, area_mean: float = 31250.0,
     pop_n = [[pops[8 * a + k].n for k in range(8)] for a in range(n_areas)]
 
     w_e = Dist(W_NORMAL_SIGN, J_E, 0.1 * J_E)
-    w_i = Dist(W_NORMAL_SIGN, -G_INH * J_E, 0.1 * G_INH * J_E)
+    w_i = Dist(W_NORMAL_SIGN, -g * J_E, 0.1 * g * J_E)
     projs: List[Projection] = []
     for a in range(n_areas):
         prob = rng.uniform(0.01, 0.15, size=(8, 8))     # [target pop, source pop]
@@ -237,7 +245,7 @@ def multi_area(seed: int = 1234, n_areas: int = 32, area_mean: float = 31250.0,
             projs.append(Projection(area_first[a], e_n, area_first[b], area_n[b],
                                     Rule(RULE_FIXED_INDEGREE, k), w_e,
                                     Dist(D_NORMAL_MIN, d_ms, 0.1 * d_ms, 0.1), seed))
-    drives = [Drive(0, total, 8000.0, J_E, seed)]
+    drives = [Drive(0, total, drive_rate_hz, J_E, seed)]
     return Network(f"multi_area_{total}", pops, projs, drives, n_ranks=n_ranks)
 
 
