@@ -237,6 +237,12 @@ int snn_get_delay_table(snn_ctx* ctx, uint32_t proj_id, uint32_t* host_thr, uint
 
 int snn_stats(snn_ctx* ctx, snn_stats_t* out);
 
+/* Failure-detection self-test: runs the sort's bounded look-back wait against a
+ * predecessor status that is never published.  The wait gives up after its spin bound
+ * (a fraction of a second) and the call returns SNN_ETIMEOUT; SNN_OK would mean the
+ * bound did not trigger, SNN_ECUDA a CUDA failure.  Allocates 4 KB of device memory. */
+int snn_selftest_bounded_wait(void* cuda_stream);
+
 /* ---- allocation-free construction ----------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that cannot
  * call cudaMalloc (a host application that owns all device memory under a fixed

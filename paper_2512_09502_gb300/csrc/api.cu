@@ -1068,6 +1068,24 @@ int snn_stats(snn_ctx* c, snn_stats_t* out) {
   return SNN_OK;
 }
 
+int snn_selftest_bounded_wait(void* cuda_stream) {
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  uint64_t* status = nullptr;
+  uint32_t* err = nullptr;
+  if (cudaMalloc(&status, 2 * 256 * sizeof(uint64_t)) != cudaSuccess) return SNN_ENOMEM;
+  if (cudaMalloc(&err, 4) != cudaSuccess) { cudaFree(status); return SNN_ENOMEM; }
+  int rc = SNN_ECUDA;
+  uint32_t h = 0;
+  if (cudaMemsetAsync(status, 0, 2 * 256 * sizeof(uint64_t), st) == cudaSuccess &&
+      cudaMemsetAsync(err, 0, 4, st) == cudaSuccess && launch_bounded_wait_selftest(status, err, st) == cudaSuccess &&
+      cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+      cudaStreamSynchronize(st) == cudaSuccess)
+    rc = (h & kErrTimeout) ? SNN_ETIMEOUT : SNN_OK;
+  cudaFree(status);
+  cudaFree(err);
+  return rc;
+}
+
 void snn_destroy(snn_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);

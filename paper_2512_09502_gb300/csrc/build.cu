@@ -216,6 +216,20 @@ __device__ __forceinline__ uint64_t look_back(const BuildArgs& a, uint64_t tile,
   }
 }
 
+// Self-test of the bounded wait: tile 1 looks back at tile 0, whose status is never
+// published, so every bin's wait must give up and flag kErrTimeout.
+__global__ void bounded_wait_selftest(BuildArgs a, uint32_t bins) {
+  if (threadIdx.x < bins) (void)look_back(a, 1, 0, threadIdx.x, bins, 1);
+}
+
+cudaError_t launch_bounded_wait_selftest(uint64_t* status, uint32_t* err, cudaStream_t st) {
+  BuildArgs a{};
+  a.status = status;
+  a.err = err;
+  bounded_wait_selftest<<<1, 256, 0, st>>>(a, 256);
+  return cudaGetLastError();
+}
+
 template <int RB, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint32_t pass,
                                                              const uint64_t* __restrict__ in,

@@ -197,6 +197,7 @@ constexpr uint32_t kMaxCountedRanks = 1024;
 cudaError_t launch_counted_count(const CountedArgs& c, cudaStream_t st, int num_sms);
 cudaError_t launch_counted_place(const CountedArgs& c, const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_histogram(const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_bounded_wait_selftest(uint64_t* status, uint32_t* err, cudaStream_t st);
 
 cudaError_t launch_generate(const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_bin_scan(const BuildArgs& a, cudaStream_t st);
