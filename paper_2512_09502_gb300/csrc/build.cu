@@ -37,16 +37,36 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // ---------------------------------------------------------------------------
 // generation
 // ---------------------------------------------------------------------------
+// Inverse of an integer CDF table: #{i : thr[i] <= w}.  The guide table (Chen & Asau's
+// indexed search) holds the count at the start of each 2^24-wide window of w, so the
+// search starts there and needs at most a few compares; the result equals a plain
+// binary search.
+__device__ __forceinline__ uint32_t guided_count(const uint32_t* thr, uint32_t len, const uint8_t* guide,
+                                                 uint32_t w) {
+  uint32_t c = guide[w >> 24];
+  while (c < len && thr[c] <= w) ++c;
+  return c;
+}
+
 __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
   __shared__ uint32_t s_tbl[256];
+  __shared__ uint8_t s_guide[256];
   __shared__ DevBlock s_blk;
   __shared__ DevProj s_proj;
   const int tid = threadIdx.x;
   const Geom g = a.g;
   const uint32_t passes = a.passes;
   for (int i = tid; i < MAX_PASSES * BINS; i += GEN_BLOCK) (&s_hist[0][0])[i] = 0;
+  // per-pass digit extraction on the 32-bit key (key_bits <= 32 on this path)
+  uint32_t dsh[MAX_PASSES], dmk[MAX_PASSES];
+#pragma unroll
+  for (int p = 0; p < MAX_PASSES; ++p) {
+    dsh[p] = a.pass_shift[p];
+    dmk[p] = p < (int)passes ? (1u << a.pass_bits[p]) - 1 : 0u;
+  }
+  const bool hist = a.fuse_hist && g.key_bits <= 32;
 
   const uint64_t per = (a.n_gen_tiles + gridDim.x - 1) / gridDim.x;
   const uint64_t t0 = (uint64_t)blockIdx.x * per;
@@ -81,20 +101,26 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
     if (P.d_kind == 1)
       for (uint32_t i = tid; i < P.d_tbl_len; i += GEN_BLOCK) s_tbl[i] = a.dtables[P.d_tbl_off + i];
     __syncthreads();
+    if (P.d_kind == 1)
+      s_guide[tid] = (uint8_t)upper_bound_u32(s_tbl, P.d_tbl_len, (uint32_t)tid << 24);   // 256 threads
+    __syncthreads();
 
     const uint64_t e0 = (tile - blk.tile_first) * (uint64_t)GEN_TILE;
     const uint32_t n = (uint32_t)min((uint64_t)GEN_TILE, blk.count - e0);
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    // fixed in-degree: (target m, k) of this thread's first item, then incremental
+    uint64_t m = 0;
+    uint32_t k = 0;
+    if (P.rule == kRuleFixedIndegree) {
+      const uint64_t e = e0 + tid;
+      m = div_magic(e, P.K, P.magic_div);
+      k = (uint32_t)(e - m * P.K);
+    }
+    const uint64_t cstep = (uint64_t)blk.tstep * P.K;
+    uint64_t cm = ((uint64_t)blk.ti0 + m * blk.tstep) * P.K;   // counter of (target m, k = 0)
     for (uint32_t i = tid; i < n; i += GEN_BLOCK) {
       const uint64_t e = e0 + i;
-      uint64_t c;
-      if (P.rule == kRuleFixedIndegree) {
-        const uint64_t m = div_magic(e, P.K, P.magic_div);
-        const uint64_t k = e - m * P.K;
-        c = ((uint64_t)blk.ti0 + m * blk.tstep) * P.K + k;
-      } else {
-        c = e;   // fixed total on one rank: draws in order
-      }
+      const uint64_t c = P.rule == kRuleFixedIndegree ? cm + k : e;   // fixed total on one rank: draws
       const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id,
                                                kPurposeSynapse), key);
       const uint32_t src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
@@ -105,14 +131,25 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       }
       const uint32_t slot = sig == blk.rank ? 0u : (sig < blk.rank ? sig + 1 : sig);
       uint32_t d = P.d_const;
-      if (P.d_kind == 1) d += upper_bound_u32(s_tbl, P.d_tbl_len, b.y);
+      if (P.d_kind == 1) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
       const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
       a.rec_a[blk.out_base + e] = (kk << g.cbits) | ((P.cbase + c) & cmask);
-      if (a.fuse_hist) {
+      if (hist) {
+        const uint32_t k32 = (uint32_t)kk;
 #pragma unroll
         for (int p = 0; p < MAX_PASSES; ++p)
-          if (p < (int)passes)
-            atomicAdd(&s_hist[p][(kk >> a.pass_shift[p]) & ((1u << a.pass_bits[p]) - 1)], 1u);
+          if (dmk[p]) atomicAdd(&s_hist[p][(k32 >> dsh[p]) & dmk[p]], 1u);
+      } else if (a.fuse_hist) {
+#pragma unroll
+        for (int p = 0; p < MAX_PASSES; ++p)
+          if (dmk[p]) atomicAdd(&s_hist[p][(uint32_t)(kk >> dsh[p]) & dmk[p]], 1u);
+      }
+      if (P.rule == kRuleFixedIndegree) {        // advance to item i + GEN_BLOCK
+        k += GEN_BLOCK;
+        while (k >= P.K) {
+          k -= (uint32_t)P.K;
+          cm += cstep;
+        }
       }
     }
   }
@@ -335,7 +372,10 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
 #pragma unroll
   for (int q = 0; q < BPT; ++q) {
     const int b = tid * BPT + q;
-    if (b < BINS) sm.binstart[b] = run;
+    if (b < BINS) {
+      sm.binstart[b] = run;
+      sm.gbase[b] -= run;          // global position of staged element k of bin b = gbase + k
+    }
     run += tot[q];
   }
   __syncthreads();
@@ -352,7 +392,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
     const uint64_t r = sm.stage[k];
     const uint32_t d = (uint32_t)((r >> shift) & dmask);
-    const uint64_t gpos = sm.gbase[d] + (k - sm.binstart[d]);
+    const uint64_t gpos = sm.gbase[d] + k;
     if (gpos < seg_end) out[gpos] = r; else atomicOr(a.err, kErrBounds);
   }
 }
