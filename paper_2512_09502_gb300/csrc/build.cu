@@ -211,7 +211,7 @@ struct SortSmem {
   static constexpr int NW = SORT_BLOCK / 32;
   uint64_t stage[SORT_BLOCK * ITEMS];
   uint64_t gbase[BINS];
-  uint32_t whist[NW][BINS];
+  uint32_t whist[2 * NW][BINS];   // two rows per warp: first and second half of its items
   uint32_t binstart[BINS];
   uint32_t wsum[NW];
   uint32_t tile;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) sm.tile = atomicAdd(&a.counters[pass], 1u);
-  for (int i = tid; i < NW * BINS; i += SORT_BLOCK) (&sm.whist[0][0])[i] = 0;
+  for (int i = tid; i < 2 * NW * BINS; i += SORT_BLOCK) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
   const uint64_t tile = sm.tile;
   if (tile >= a.n_sort_tiles) return;
@@ -302,20 +302,35 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     const uint32_t idx = wbase + j * 32 + lane;
     rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
+  // Stable warp-level ranking.  The warp's items j < H and j >= H count into two
+  // separate histogram rows (2w, 2w + 1), which keeps record order (row 2w holds the
+  // warp's first 32H records) and runs the two read-modify-write chains side by side.
+  constexpr int H = ITEMS / 2;
+  static_assert(ITEMS % 2 == 0, "two histogram rows per warp");
   const uint32_t lt = (1u << lane) - 1;
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t idx = wbase + j * 32 + lane;
-    const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (lane == leader && d < BINS) {
-      old = sm.whist[warp][d];
-      sm.whist[warp][d] = old + __popc(peers);
+  for (int jj = 0; jj < H; ++jj) {
+    uint32_t d[2], peers[2], old[2];
+    int leader[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int j = jj + v * H;
+      const uint32_t idx = wbase + j * 32 + lane;
+      d[v] = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
+      peers[v] = __match_any_sync(0xffffffffu, d[v]);
+      leader[v] = __ffs(peers[v]) - 1;
     }
-    old = __shfl_sync(0xffffffffu, old, leader);
-    rnk[j] = old + __popc(peers & lt);
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+      old[v] = (lane == leader[v] && d[v] < BINS) ? sm.whist[2 * warp + v][d[v]] : 0u;
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+      if (lane == leader[v] && d[v] < BINS) sm.whist[2 * warp + v][d[v]] = old[v] + __popc(peers[v]);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      old[v] = __shfl_sync(0xffffffffu, old[v], leader[v]);
+      rnk[jj + v * H] = old[v] + __popc(peers[v] & lt);
+    }
     __syncwarp();
   }
   __syncthreads();
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     uint32_t t = 0;
     if (b < BINS) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
+      for (int w = 0; w < 2 * NW; ++w) {
         const uint32_t c = sm.whist[w][b];
         sm.whist[w][b] = t;
         t += c;
@@ -345,17 +360,6 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     const int b = tid * BPT + q;
     if (b < BINS) st_status(strow + b, (first ? ST_INC : ST_AGG) | ep | tot[q]);
   }
-#pragma unroll
-  for (int q = 0; q < BPT; ++q) {
-    const int b = tid * BPT + q;
-    if (b >= BINS) continue;
-    uint64_t excl = 0;
-    if (!first) {
-      excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
-      st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
-    }
-    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * kHistStride + b] + excl;
-  }
 
   // tile-local exclusive scan of the bin counts (thread-contiguous bins)
   uint32_t incl = tsum;
@@ -368,25 +372,38 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
   __syncthreads();
   uint32_t woff = 0;
   for (int w = 0; w < warp; ++w) woff += sm.wsum[w];
+  uint32_t bstart[BPT];
   uint32_t run = woff + incl - tsum;
 #pragma unroll
   for (int q = 0; q < BPT; ++q) {
     const int b = tid * BPT + q;
-    if (b < BINS) {
-      sm.binstart[b] = run;
-      sm.gbase[b] -= run;          // global position of staged element k of bin b = gbase + k
-    }
+    bstart[q] = run;
+    if (b < BINS) sm.binstart[b] = run;
     run += tot[q];
   }
   __syncthreads();
 
+  // staging in shared memory needs only tile-local offsets, so it runs before the
+  // look-back: the predecessors get that much longer to publish inclusive prefixes
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     if (idx < n) {
       const uint32_t d = (uint32_t)((rec[j] >> shift) & dmask);
-      sm.stage[sm.binstart[d] + sm.whist[warp][d] + rnk[j]] = rec[j];
+      sm.stage[sm.binstart[d] + sm.whist[2 * warp + (j >= H ? 1 : 0)][d] + rnk[j]] = rec[j];
     }
+  }
+#pragma unroll
+  for (int q = 0; q < BPT; ++q) {
+    const int b = tid * BPT + q;
+    if (b >= BINS) continue;
+    uint64_t excl = 0;
+    if (!first) {
+      excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
+      st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
+    }
+    // global position of staged element k of bin b = gbase[b] + k
+    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * kHistStride + b] + excl - bstart[q];
   }
   __syncthreads();
   for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
@@ -700,66 +717,125 @@ __device__ __forceinline__ float draw_weight(const DevProj& P, uint32_t w2, uint
   return P.w_mean >= 0.f ? fmaxf(w, 0.f) : fminf(w, 0.f);
 }
 
+constexpr int FIN_Q = 4;   // consecutive records per thread of the finalize kernel
+
+// Each thread decodes FIN_Q consecutive sorted records: one pair of 16-byte loads, the
+// projection lookup reused while the counters stay in one projection, and one vector
+// store per output array.  Row starts: a record whose row differs from its
+// predecessor's writes the starts of the rows in between.
 __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64_t* __restrict__ rec,
-                                                      uint64_t E) {
+                                                      uint64_t E, uint32_t vec) {
   const Geom g = a.g;
   const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
   const uint64_t smask = (1ull << g.sb) - 1;
   const uint64_t dmask = (1ull << g.db) - 1;
+  const uint64_t nq = (E + FIN_Q - 1) / FIN_Q;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
-    const uint32_t seg = g.R == 1 ? 0u : upper_bound_u64(a.seg_start + 1, g.R, i);
-    const uint64_t seg_lo = a.seg_start[seg], seg_hi = a.seg_start[seg + 1];
-    const uint64_t r = rec[i];
-    const uint64_t key = r >> g.cbits;
-    const uint64_t cidx = r & cmask;
-    const uint32_t d = (uint32_t)(key & dmask);
-    const uint32_t s = (uint32_t)((key >> g.db) & smask);
-    const uint32_t slot = (uint32_t)(key >> (g.db + g.sb));
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+    const uint64_t i0 = q * FIN_Q;
+    const bool full = vec && i0 + FIN_Q <= E;
+    uint64_t r[FIN_Q];
+    if (full) {
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(rec + i0);
+      const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(rec + i0 + 2);
+      r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < FIN_Q; ++j) r[j] = i0 + j < E ? rec[i0 + j] : 0ull;
+    }
+    uint32_t seg = g.R == 1 ? 0u : upper_bound_u64(a.seg_start + 1, g.R, i0);
+    uint64_t seg_hi = a.seg_start[seg + 1];
     const uint32_t* doff = a.dense_off + (uint64_t)seg * g.R;
-    const uint64_t row = (uint64_t)doff[slot] + s;
-    if (slot >= g.R || row >= g.N) {   // corrupt record: flag it, touch nothing
-      atomicOr(a.err, kErrBounds);
-      continue;
-    }
-    int64_t prow = -1;
-    if (i > seg_lo) {
-      const uint64_t kp = rec[i - 1] >> g.cbits;
-      prow = (int64_t)((uint64_t)doff[kp >> (g.db + g.sb)] + ((kp >> g.db) & smask));
-    }
     uint64_t* dn = a.dense + (uint64_t)seg * ((uint64_t)g.N + 1);
-    for (int64_t x = prow + 1; x <= (int64_t)row; ++x) dn[x] = i;
-    if (i == seg_hi - 1)
-      for (uint64_t x = row + 1; x <= g.N; ++x) dn[x] = seg_hi;
-
-    // projection of the counter, then target and weight regenerated from it
-    const uint32_t p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
-    const DevProj& P = a.projs[p];
-    const uint64_t c = cidx - P.cbase;
-    uint32_t t;
-    if (P.rule == kRuleFixedIndegree) {
-      t = P.tgt_first + (uint32_t)div_magic(c, P.K, P.magic_div) * P.tgt_stride;
-    } else if (P.rule == kRuleFixedTotal) {
-      const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);
-      t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
-    } else {
-      t = P.tgt_first + (uint32_t)div_magic(c, P.n_src, P.magic_div) * P.tgt_stride;
+    int64_t prow = -1;
+    if (i0 > a.seg_start[seg]) {
+      const uint64_t kp = rec[i0 - 1] >> g.cbits;
+      const uint32_t ps = (uint32_t)(kp >> (g.db + g.sb));
+      prow = ps < g.R ? (int64_t)((uint64_t)doff[ps] + ((kp >> g.db) & smask)) : (int64_t)g.N;
     }
-    const uint32_t tl = g.R == 1 ? t : (uint32_t)div_magic(t, g.R, g.magic_R);
-    const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
-    const float w = draw_weight(P, b.z, b.w);
-    a.tgt[i] = tl;
-    a.d[i] = (uint8_t)d;
-    if (a.w_format == 0) {
-      ((float*)a.w)[i] = w;
-    } else if (a.w_format == 1) {
-      ((__nv_bfloat16*)a.w)[i] = __float2bfloat16_rn(w);
+    uint32_t p = 0;
+    uint64_t p_lo = 0, p_hi = 0;   // counters [p_lo, p_hi) of the cached projection p (none yet)
+    uint32_t tl[FIN_Q], wb[FIN_Q], dd[FIN_Q];
+    bool ok[FIN_Q];
+#pragma unroll
+    for (int j = 0; j < FIN_Q; ++j) {
+      const uint64_t i = i0 + j;
+      ok[j] = false;
+      tl[j] = 0; wb[j] = 0; dd[j] = 0;
+      if (i >= E) continue;
+      while (i >= seg_hi) {          // first record of a later segment
+        ++seg;
+        seg_hi = a.seg_start[seg + 1];
+        doff = a.dense_off + (uint64_t)seg * g.R;
+        dn = a.dense + (uint64_t)seg * ((uint64_t)g.N + 1);
+        prow = -1;
+      }
+      const uint64_t key = r[j] >> g.cbits;
+      const uint64_t cidx = r[j] & cmask;
+      const uint32_t d = (uint32_t)(key & dmask);
+      const uint32_t s = (uint32_t)((key >> g.db) & smask);
+      const uint32_t slot = (uint32_t)(key >> (g.db + g.sb));
+      const uint64_t row = slot < g.R ? (uint64_t)doff[slot] + s : (uint64_t)g.N;
+      if (row >= g.N) {              // corrupt record: flag it, write nothing for it
+        atomicOr(a.err, kErrBounds);
+        prow = (int64_t)g.N;
+        continue;
+      }
+      for (int64_t x = prow + 1; x <= (int64_t)row; ++x) dn[x] = i;
+      if (i == seg_hi - 1)
+        for (uint64_t x = row + 1; x <= g.N; ++x) dn[x] = seg_hi;
+      prow = (int64_t)row;
+
+      // projection of the counter, then target and weight regenerated from it
+      if (cidx - p_lo >= p_hi - p_lo) {
+        p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
+        p_lo = a.cbase_sorted[p];
+        p_hi = p + 1 < a.nproj ? a.cbase_sorted[p + 1] : ~0ull;
+      }
+      const DevProj& P = a.projs[p];
+      const uint64_t c = cidx - P.cbase;
+      uint32_t t;
+      if (P.rule == kRuleFixedIndegree) {
+        t = P.tgt_first + (uint32_t)div_magic(c, P.K, P.magic_div) * P.tgt_stride;
+      } else if (P.rule == kRuleFixedTotal) {
+        const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);
+        t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
+      } else {
+        t = P.tgt_first + (uint32_t)div_magic(c, P.n_src, P.magic_div) * P.tgt_stride;
+      }
+      tl[j] = g.R == 1 ? t : (uint32_t)div_magic(t, g.R, g.magic_R);
+      dd[j] = d;
+      const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
+      const float w = draw_weight(P, b.z, b.w);
+      if (a.w_format == 0) {
+        wb[j] = __float_as_uint(w);
+      } else if (a.w_format == 1) {
+        wb[j] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+      } else {
+        const uint32_t sig = slot != 0 ? (slot <= seg ? slot - 1 : slot) : seg;
+        const uint64_t src_gid = (uint64_t)s * g.R + sig;
+        const float sc = a.row_scale_src ? a.row_scale_src[src_gid] : 1.0f;
+        wb[j] = __half_as_ushort(__float2half_rn(w / sc));
+      }
+      ok[j] = true;
+    }
+    if (full && ok[0] && ok[1] && ok[2] && ok[3]) {
+      *reinterpret_cast<uint4*>(a.tgt + i0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+      *reinterpret_cast<uint32_t*>(a.d + i0) = dd[0] | (dd[1] << 8) | (dd[2] << 16) | (dd[3] << 24);
+      if (a.w_format == 0)
+        *reinterpret_cast<uint4*>((uint32_t*)a.w + i0) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+      else
+        *reinterpret_cast<uint2*>((uint16_t*)a.w + i0) = make_uint2(wb[0] | (wb[1] << 16), wb[2] | (wb[3] << 16));
     } else {
-      uint32_t sig = 0, src_s = s;
-      if (slot != 0) sig = slot <= seg ? slot - 1 : slot; else sig = seg;
-      const uint64_t src_gid = (uint64_t)src_s * g.R + sig;
-      const float sc = a.row_scale_src ? a.row_scale_src[src_gid] : 1.0f;
-      ((__half*)a.w)[i] = __float2half_rn(w / sc);
+#pragma unroll
+      for (int j = 0; j < FIN_Q; ++j) {
+        if (!ok[j]) continue;
+        const uint64_t i = i0 + j;
+        a.tgt[i] = tl[j];
+        a.d[i] = (uint8_t)dd[j];
+        if (a.w_format == 0) ((uint32_t*)a.w)[i] = wb[j];
+        else ((uint16_t*)a.w)[i] = (uint16_t)wb[j];
+      }
     }
   }
 }
@@ -780,8 +856,11 @@ cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E,
                         st>>>(a.dense, a.seg_start, a.g.R, a.g.N);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || E == 0) return e;
-  const uint64_t grid = std::min<uint64_t>((E + 255) / 256, (uint64_t)a.num_sms * 16);
-  finalize_kernel<<<(unsigned)grid, 256, 0, st>>>(a, rec, E);
+  const uint64_t nq = (E + FIN_Q - 1) / FIN_Q;
+  const uint64_t grid = std::min<uint64_t>((nq + 255) / 256, (uint64_t)a.num_sms * 16);
+  // vector loads and stores need 16-byte aligned bases (quad starts are multiples of 4)
+  const uint32_t vec = (((uintptr_t)rec | (uintptr_t)a.tgt | (uintptr_t)a.w | (uintptr_t)a.d) & 15u) == 0;
+  finalize_kernel<<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
   return cudaGetLastError();
 }
 

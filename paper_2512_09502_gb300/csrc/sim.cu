@@ -26,7 +26,7 @@
 namespace snn {
 
 constexpr int UPD_BLOCK = 256;
-constexpr int UPD_ILP = 4;        // neurons per thread per iteration (loads issued together)
+constexpr int UPD_ILP = 2;        // neurons per thread per iteration (loads issued together)
 constexpr int DEL_BLOCK = 256;
 constexpr int DEL_ILP = 4;        // events per thread per iteration
 constexpr uint32_t MAX_SMEM_DRIVES = 16;
@@ -60,46 +60,78 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
   for (uint64_t base = (uint64_t)blockIdx.x * UPD_BLOCK * UPD_ILP; base < a.N; base += stride) {
     float V[UPD_ILP], Iex[UPD_ILP], Iin[UPD_ILP], in_ex[UPD_ILP], in_in[UPD_ILP];
     uint32_t refr[UPD_ILP], pi[UPD_ILP], gid[UPD_ILP];
-    bool spike[UPD_ILP];
-    // phase 1: every load of the four neurons
+    bool spike[UPD_ILP], live[UPD_ILP];
+    // phase 1: every load of the neurons (I_in is identically 0 with a merged ring)
 #pragma unroll
     for (int k = 0; k < UPD_ILP; ++k) {
       const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
-      if (i < a.N) {
-        V[k] = a.V[i]; Iex[k] = a.Iex[i]; Iin[k] = a.Iin[i];
+      live[k] = i < a.N;
+      if (live[k]) {
+        V[k] = a.V[i]; Iex[k] = a.Iex[i];
+        Iin[k] = a.n_rec == 2 ? a.Iin[i] : 0.f;
         refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
         in_ex[k] = rex[i];
         in_in[k] = a.n_rec == 2 ? rin[i] : 0.f;
         gid[k] = a.R == 1 ? (uint32_t)i : a.gid_of[i];
       }
     }
-    // phase 2: integrate (independent chains, interleaved by the compiler)
+    // phase 2: propagate state and synaptic input (independent chains)
+    float thr[UPD_ILP], vre[UPD_ILP];
+    uint32_t rst[UPD_ILP];
 #pragma unroll
     for (int k = 0; k < UPD_ILP; ++k) {
-      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
-      spike[k] = false;
-      if (i < a.N) {
+      if (live[k]) {
         const DevPop P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
         float v = V[k], ie = Iex[k], ii = Iin[k];
         uint32_t rf = refr[k];
         if (rf == 0) v = P.P22 * v + P.P21ex * ie + P.P21in * ii + P.P20 * P.Ie;
         else --rf;
-        ie = P.P11ex * ie + in_ex[k];
-        ii = P.P11in * ii + in_in[k];
-        for (uint32_t q = 0; q < a.ndrives; ++q) {
-          const DevDrive dr = q < MAX_SMEM_DRIVES ? s_dr[q] : a.drives[q];
-          if (gid[k] - dr.first < dr.n) {
-            const uint4 b = philox_stream((uint64_t)gid[k] | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
-            const uint32_t cnt = table_count(s_tbl + dr.tbl_off, dr.tbl_len, b.x);
-            if (dr.weight >= 0.f || a.n_rec == 1) ie += (float)cnt * dr.weight; else ii += (float)cnt * dr.weight;
-          }
+        Iex[k] = P.P11ex * ie + in_ex[k];
+        Iin[k] = P.P11in * ii + in_in[k];
+        V[k] = v; refr[k] = rf;
+        thr[k] = P.Vth; vre[k] = P.Vreset; rst[k] = P.ref_steps;
+      }
+    }
+    // Poisson drives, in drive order: the neurons' draws are issued together and one
+    // pass over the (ascending) count thresholds serves all of them
+    for (uint32_t q = 0; q < a.ndrives; ++q) {
+      const DevDrive dr = q < MAX_SMEM_DRIVES ? s_dr[q] : a.drives[q];
+      uint32_t wd[UPD_ILP], cnt[UPD_ILP];
+      bool in[UPD_ILP];
+      uint32_t wmax = 0;
+#pragma unroll
+      for (int k = 0; k < UPD_ILP; ++k) {
+        in[k] = live[k] && gid[k] - dr.first < dr.n;
+        wd[k] = in[k] ? philox_stream((uint64_t)gid[k] | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed).x : 0u;
+        cnt[k] = 0;
+        wmax = wd[k] > wmax ? wd[k] : wmax;
+      }
+      const uint32_t* tb = s_tbl + dr.tbl_off;
+      if (dr.tbl_len <= 32) {
+        for (uint32_t j = 0; j < dr.tbl_len; ++j) {
+          const uint32_t t = tb[j];
+          if (t > wmax) break;
+#pragma unroll
+          for (int k = 0; k < UPD_ILP; ++k) cnt[k] += t <= wd[k] ? 1u : 0u;
         }
-        if (v >= P.Vth) {
-          v = P.Vreset;
-          rf = P.ref_steps;
-          spike[k] = true;
-        }
-        V[k] = v; Iex[k] = ie; Iin[k] = ii; refr[k] = rf;
+      } else {
+#pragma unroll
+        for (int k = 0; k < UPD_ILP; ++k) cnt[k] = upper_bound_u32(tb, dr.tbl_len, wd[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < UPD_ILP; ++k) {
+        if (!in[k]) continue;
+        if (dr.weight >= 0.f || a.n_rec == 1) Iex[k] += (float)cnt[k] * dr.weight;
+        else Iin[k] += (float)cnt[k] * dr.weight;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPD_ILP; ++k) {
+      spike[k] = false;
+      if (live[k] && V[k] >= thr[k]) {
+        V[k] = vre[k];
+        refr[k] = rst[k];
+        spike[k] = true;
       }
     }
     // phase 3: stores, ring slot cleared, spikes appended
@@ -109,7 +141,7 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
       if (i < a.N) {
         a.V[i] = V[k];
         a.Iex[i] = Iex[k];
-        a.Iin[i] = Iin[k];
+        if (a.n_rec == 2) a.Iin[i] = Iin[k];
         a.refr[i] = (uint16_t)refr[k];
         rex[i] = 0.f;
         if (a.n_rec == 2) rin[i] = 0.f;
@@ -132,11 +164,13 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
         const uint32_t off = __popc(mask & ((1u << lane) - 1));
         if (spike[k]) {
           a.spk[(uint64_t)(n & 1) * a.N + sbase + off] = (uint32_t)i;
-          unsigned long long lb = 0;
-          if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
-          lb = __shfl_sync(mask, lb, leader);
-          const unsigned long long ls = lb + off;
-          if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid[k]);
+          if (a.log_cap) {
+            unsigned long long lb = 0;
+            if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
+            lb = __shfl_sync(mask, lb, leader);
+            const unsigned long long ls = lb + off;
+            if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid[k]);
+          }
         }
       }
     }
