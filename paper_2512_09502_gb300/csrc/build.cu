@@ -30,6 +30,7 @@ namespace snn {
 constexpr int GEN_BLOCK = 256;
 constexpr int GEN_TILE = 4096;
 constexpr int SORT_BLOCK = 256;
+constexpr int SORT_MIN_CTAS = 3;       // resident sort CTAs per SM the register budget targets
 constexpr int MAX_PASSES = 6;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
@@ -211,7 +212,7 @@ struct SortSmem {
   static constexpr int NW = SORT_BLOCK / 32;
   uint64_t stage[SORT_BLOCK * ITEMS];
   uint64_t gbase[BINS];
-  uint32_t whist[2 * NW][BINS];   // two rows per warp: first and second half of its items
+  uint32_t whist[NW][BINS];
   uint32_t binstart[BINS];
   uint32_t wsum[NW];
   uint32_t tile;
@@ -268,20 +269,20 @@ cudaError_t launch_bounded_wait_selftest(uint64_t* status, uint32_t* err, cudaSt
 }
 
 template <int RB, int ITEMS>
-__global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint32_t pass,
+__global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(BuildArgs a, uint32_t pass,
                                                              const uint64_t* __restrict__ in,
                                                              uint64_t* __restrict__ out,
                                                              uint32_t epoch) {
   constexpr int BINS = 1 << RB;
   constexpr int NW = SORT_BLOCK / 32;
-  constexpr int BPT = BINS >= SORT_BLOCK ? BINS / SORT_BLOCK : 1;   // bins per thread
+  constexpr int BPT = (BINS + SORT_BLOCK - 1) / SORT_BLOCK;   // bins per thread
   constexpr int TILE = SORT_BLOCK * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem<RB, ITEMS>& sm = *reinterpret_cast<SortSmem<RB, ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) sm.tile = atomicAdd(&a.counters[pass], 1u);
-  for (int i = tid; i < 2 * NW * BINS; i += SORT_BLOCK) (&sm.whist[0][0])[i] = 0;
+  for (int i = tid; i < NW * BINS; i += SORT_BLOCK) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
   const uint64_t tile = sm.tile;
   if (tile >= a.n_sort_tiles) return;
@@ -302,35 +303,29 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     const uint32_t idx = wbase + j * 32 + lane;
     rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
-  // Stable warp-level ranking.  The warp's items j < H and j >= H count into two
-  // separate histogram rows (2w, 2w + 1), which keeps record order (row 2w holds the
-  // warp's first 32H records) and runs the two read-modify-write chains side by side.
-  constexpr int H = ITEMS / 2;
-  static_assert(ITEMS % 2 == 0, "two histogram rows per warp");
+  // Stable warp-level ranking: item j's peers (lanes holding the same digit) come from
+  // one ballot per digit bit, plus one for the out-of-range marker; the leader of each
+  // peer group advances the warp's running count of that digit.
   const uint32_t lt = (1u << lane) - 1;
 #pragma unroll
-  for (int jj = 0; jj < H; ++jj) {
-    uint32_t d[2], peers[2], old[2];
-    int leader[2];
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t idx = wbase + j * 32 + lane;
+    const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
+    uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int j = jj + v * H;
-      const uint32_t idx = wbase + j * 32 + lane;
-      d[v] = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
-      peers[v] = __match_any_sync(0xffffffffu, d[v]);
-      leader[v] = __ffs(peers[v]) - 1;
+    for (int bit = 0; bit <= RB; ++bit) {
+      const bool set = (d >> bit) & 1u;
+      const uint32_t bl = __ballot_sync(0xffffffffu, set);
+      peers &= set ? bl : ~bl;
     }
-#pragma unroll
-    for (int v = 0; v < 2; ++v)
-      old[v] = (lane == leader[v] && d[v] < BINS) ? sm.whist[2 * warp + v][d[v]] : 0u;
-#pragma unroll
-    for (int v = 0; v < 2; ++v)
-      if (lane == leader[v] && d[v] < BINS) sm.whist[2 * warp + v][d[v]] = old[v] + __popc(peers[v]);
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      old[v] = __shfl_sync(0xffffffffu, old[v], leader[v]);
-      rnk[jj + v * H] = old[v] + __popc(peers[v] & lt);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && d < BINS) {
+      old = sm.whist[warp][d];
+      sm.whist[warp][d] = old + __popc(peers);
     }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rnk[j] = old + __popc(peers & lt);
     __syncwarp();
   }
   __syncthreads();
@@ -343,7 +338,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     uint32_t t = 0;
     if (b < BINS) {
 #pragma unroll
-      for (int w = 0; w < 2 * NW; ++w) {
+      for (int w = 0; w < NW; ++w) {
         const uint32_t c = sm.whist[w][b];
         sm.whist[w][b] = t;
         t += c;
@@ -390,7 +385,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) onesweep_pass(BuildArgs a, uint
     const uint32_t idx = wbase + j * 32 + lane;
     if (idx < n) {
       const uint32_t d = (uint32_t)((rec[j] >> shift) & dmask);
-      sm.stage[sm.binstart[d] + sm.whist[2 * warp + (j >= H ? 1 : 0)][d] + rnk[j]] = rec[j];
+      sm.stage[sm.binstart[d] + sm.whist[warp][d] + rnk[j]] = rec[j];
     }
   }
 #pragma unroll
