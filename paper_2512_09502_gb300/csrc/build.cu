@@ -29,8 +29,8 @@ namespace snn {
 
 constexpr int GEN_BLOCK = 256;
 constexpr int GEN_TILE = 4096;
-constexpr int SORT_BLOCK = 256;
-constexpr int SORT_MIN_CTAS = 3;       // resident sort CTAs per SM the register budget targets
+constexpr int SORT_BLOCK = 512;
+constexpr int SORT_MIN_CTAS = 2;       // resident sort CTAs per SM (64 registers: 32 warps)
 constexpr int MAX_PASSES = 6;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
@@ -219,12 +219,12 @@ struct SortSmem {
 };
 
 // Exclusive prefix of bin b over the predecessor tiles of this segment: sum the
-// aggregates of earlier tiles until one carries an inclusive prefix.  Eight status
+// aggregates of earlier tiles until one carries an inclusive prefix.  Four status
 // words are requested per round trip; a word that is not ready yet is polled with a
 // bounded wait (a global error flag short-cuts every other wait once one gave up).
 __device__ __forceinline__ uint64_t look_back(const BuildArgs& a, uint64_t tile, uint64_t first_tile,
                                               uint32_t b, uint32_t bins, uint32_t epoch) {
-  constexpr int W = 8;
+  constexpr int W = 4;
   const uint64_t ep = (uint64_t)(epoch & 0xFFFF) << 46;
   uint64_t excl = 0;
   uint64_t k = tile - 1;                    // tile > first_tile here

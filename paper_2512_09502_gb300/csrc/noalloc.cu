@@ -30,7 +30,7 @@ namespace {
 constexpr uint64_t kMaxSynapses = SNN_NOALLOC_MAX_SYNAPSES;
 constexpr uint32_t kBins = 256;            // radix 8 (the only sort width built)
 constexpr uint32_t kMaxPasses = 6;
-constexpr uint64_t kTile = 4096;           // sort tile: 256 threads x 16 records
+constexpr uint64_t kTile = 4096;           // records per sort tile the scratch is sized for
 constexpr uint64_t kMaxTiles = (kMaxSynapses + kTile - 1) / kTile;
 
 struct Scratch {
@@ -220,7 +220,10 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   a.tgt = dev_tgt; a.w = dev_w; a.d = dev_d; a.w_format = 0;
   a.dense = dev_row_ptr; a.row_scale_src = nullptr;
   a.fuse_hist = 1;
-  a.sort_items = 16;
+  a.sort_items = 0;                        // records per thread giving kTile-record tiles
+  for (uint32_t it : {8u, 12u, 16u})
+    if (sort_tile_items(it) == kTile) a.sort_items = it;
+  if (a.sort_items == 0) NA_FAIL(SNN_ECUDA, "no sort tile shape of %llu records", (unsigned long long)kTile);
   for (int p = 0; p < 8; ++p) { a.pass_bits[p] = pass_bits[p]; a.pass_shift[p] = pass_shift[p]; }
 
   NA_CK(launch_generate(a, st));
