@@ -36,7 +36,8 @@ METRIC = "synapses built/s + synaptic events/s (1 GB300, % HBM peak), bf16 vs fp
 UNIT = "(synapses + events)/s"
 # algorithmic bytes per unit of the measured kernels
 BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize": 17.0, "generate": 8.0,
-         "update": 38.0}
+         "update": 38.0, "update_merged": 30.0}   # update: V, I_ex, I_in, refr r/w, pop r, ring r + clear;
+                                                  # merged ring (tau_ex == tau_in): no I_in traffic
 
 
 WORKLOADS = ("balanced_500k", "balanced_5k", "multi_area", "multi_area_r128")
@@ -303,7 +304,9 @@ def run_ours(args):
                               units=E, bpu=BYTES["sort_pass"], bound="hbm"),
         "finalize_kernel": dict(ms=prof["t_finalize_ms"], launches=1, units=E, bpu=BYTES["finalize"], bound="hbm"),
         "update_kernel": dict(ms=prof["t_update_ms"] / max(prof["update_launches"], 1), launches=args.sim_steps,
-                              units=net.n_neurons, bpu=BYTES["update"], bound="hbm"),
+                              units=net.n_neurons, bound="hbm",
+                              bpu=BYTES["update_merged" if all(p.params.tau_syn_ex == p.params.tau_syn_in
+                                                               for p in net.populations) else "update"]),
         "deliver_kernel": dict(ms=prof["t_deliver_ms"] / dl, launches=args.sim_steps, units=ev_launch,
                                bpu=BYTES["deliver_f32"], bound="hbm"),
     }

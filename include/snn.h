@@ -81,7 +81,9 @@ extern "C" {
 typedef struct snn_ctx snn_ctx;
 
 typedef struct snn_allocator {
-  /* Return device memory of at least `bytes` bytes usable on `stream`, or NULL. */
+  /* Return device memory of at least `bytes` bytes usable on `stream`, or NULL.  The
+     pointer must be 16-byte aligned (kernels use 16-byte vector accesses); a
+     misaligned pointer is released again and the call that asked fails with ENOMEM. */
   void* (*alloc)(void* user, size_t bytes, void* stream);
   /* Release memory obtained from alloc. */
   void (*free)(void* user, void* ptr, size_t bytes, void* stream);

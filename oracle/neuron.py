@@ -15,7 +15,8 @@ Step n of each neuron (reading; the paper is silent on the update order):
   1. not refractory: V <- P22 V + P21_ex I_ex + P21_in I_in + P20 I_e;
      refractory: the counter decreases and V stays at V_reset;
   2. I_x <- P11_x I_x + ring[n mod D][x]; the slot is cleared; a Poisson drive adds
-     k J with k drawn from the Poisson table (stream POISSON, counter (gid, n));
+     k J with k drawn from the Poisson table: word (gid mod 4) of the POISSON-stream
+     block with counter (gid div 4, n), so four consecutive neurons share one block;
   3. V >= V_th: V <- V_reset, refractory for round(t_ref / h) steps, spike (n, gid).
 Spike delivery (Appendix, point-to-point example, delivery figure): a spike of step n
 through a connection of delay d (>= 1 step) and weight w adds w to slot (n + d) mod D
@@ -123,9 +124,7 @@ class Simulator:
         self.Iin = c["P11_in"] * self.Iin + self.ring[slot, 1]
         self.ring[slot] = 0.0
         for di, (dr, thr) in enumerate(self.drives):
-            g = np.arange(dr.first, dr.first + dr.n, dtype=np.uint64)
-            ctr = g | (np.uint64(n) << np.uint64(32))
-            k = sm.inverse_table(thr, ph.stream(ctr, di, ph.PURPOSE_POISSON, dr.seed)[0])
+            k = poisson_counts(thr, di, dr.seed, dr.first, dr.n, n)
             if dr.weight >= 0:
                 self.Iex[dr.first:dr.first + dr.n] += k * dr.weight
             else:
@@ -155,6 +154,16 @@ class Simulator:
             if record_v:
                 vs.append(self.V.copy())
         return spikes, (np.array(vs) if record_v else None)
+
+
+def poisson_counts(thr, drive_index: int, seed: int, first: int, n_neurons: int, step: int):
+    """Drive counts of neurons first .. first + n_neurons - 1 at step ``step``: neuron g
+    inverts word (g mod 4) of the POISSON block with counter (g div 4, step) through the
+    count table ``thr``."""
+    g = np.arange(first, first + n_neurons, dtype=np.uint64)
+    ctr = (g >> np.uint64(2)) | (np.uint64(step) << np.uint64(32))
+    words = ph.stream(ctr, drive_index, ph.PURPOSE_POISSON, seed)
+    return sm.inverse_table(thr, np.choose((g & np.uint64(3)).astype(np.int64), words))
 
 
 def ring_slots_for(max_delay: int) -> int:

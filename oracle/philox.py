@@ -31,7 +31,7 @@ MASK = np.uint64(0xFFFFFFFF)
 PURPOSE_SYNAPSE = 0      # source choice, delay, weight of one synapse / draw
 PURPOSE_FT_TARGET = 1    # target choice of a fixed-total draw
 PURPOSE_PB_TEST = 2      # inclusion test of pairwise Bernoulli (4 pairs per call)
-PURPOSE_POISSON = 3      # Poisson drive count of one neuron in one step
+PURPOSE_POISSON = 3      # Poisson drive counts of four consecutive neurons in one step
 PURPOSE_VINIT = 4        # initial membrane potential
 
 

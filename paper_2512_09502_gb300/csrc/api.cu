@@ -118,6 +118,10 @@ void* dalloc(snn_ctx* c, size_t bytes) {
   void* p = nullptr;
   if (c->alloc.alloc) {
     p = c->alloc.alloc(c->alloc.user, bytes, (void*)c->st);
+    if (p && ((uintptr_t)p & 15u)) {          // vector accesses need 16-byte alignment
+      if (c->alloc.free) c->alloc.free(c->alloc.user, p, bytes, (void*)c->st);
+      p = nullptr;
+    }
   } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -749,8 +753,9 @@ int snn_calibrate(snn_ctx* c) {
   bool merged = true;
   for (const auto& ps : c->pops) merged = merged && ps.p.tau_syn_ex == ps.p.tau_syn_in;
   s.n_rec = merged ? 1 : 2;
-  AL(s.ring, (uint64_t)D * s.n_rec * N, "ring buffers");
-  CK(cudaMemsetAsync(s.ring, 0, (size_t)D * s.n_rec * N * 4, c->st));
+  s.ring_stride = (N + 3u) & ~3u;
+  AL(s.ring, (uint64_t)D * s.n_rec * s.ring_stride, "ring buffers");
+  CK(cudaMemsetAsync(s.ring, 0, (size_t)D * s.n_rec * s.ring_stride * 4, c->st));
   s.ring_mask = D - 1;
   AL(s.step, 1, "step");
   AL(s.n_spk, 2, "spike counts");

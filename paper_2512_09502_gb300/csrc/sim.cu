@@ -26,7 +26,7 @@
 namespace snn {
 
 constexpr int UPD_BLOCK = 256;
-constexpr int UPD_ILP = 2;        // neurons per thread per iteration (loads issued together)
+constexpr int UPD_Q = 4;          // consecutive neurons per thread
 constexpr int DEL_BLOCK = 256;
 constexpr int DEL_ILP = 4;        // events per thread per iteration
 constexpr uint32_t MAX_SMEM_DRIVES = 16;
@@ -41,7 +41,11 @@ __device__ __forceinline__ uint32_t table_count(const uint32_t* thr, uint32_t le
   return upper_bound_u32(thr, len, w);
 }
 
-__global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k_step) {
+// One thread updates UPD_Q = 4 consecutive neuron positions: 16-byte loads and stores
+// of the state and ring slot (the host guarantees 16-byte aligned arrays and a ring
+// stride that is a multiple of 4) and, on one rank, a single Philox block for the four
+// Poisson counts (neuron g draws word g mod 4 of the block with counter (g div 4, n)).
+__global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_t k_step) {
   __shared__ uint32_t s_tbl[256];
   __shared__ DevPop s_pop[64];
   __shared__ DevDrive s_dr[MAX_SMEM_DRIVES];
@@ -54,32 +58,63 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
   if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;   // next step's list
   __syncthreads();
   const uint32_t slot = n & a.ring_mask;
-  float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.N;
-  float* rin = rex + a.N;
-  const uint64_t stride = (uint64_t)gridDim.x * UPD_BLOCK * UPD_ILP;
-  for (uint64_t base = (uint64_t)blockIdx.x * UPD_BLOCK * UPD_ILP; base < a.N; base += stride) {
-    float V[UPD_ILP], Iex[UPD_ILP], Iin[UPD_ILP], in_ex[UPD_ILP], in_in[UPD_ILP];
-    uint32_t refr[UPD_ILP], pi[UPD_ILP], gid[UPD_ILP];
-    bool spike[UPD_ILP], live[UPD_ILP];
-    // phase 1: every load of the neurons (I_in is identically 0 with a merged ring)
+  float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.ring_stride;
+  float* rin = rex + a.ring_stride;
+  const bool two = a.n_rec == 2;
+  const uint32_t nq = (a.N + UPD_Q - 1) / UPD_Q;
+  for (uint32_t qb = blockIdx.x * UPD_BLOCK; qb < nq; qb += gridDim.x * UPD_BLOCK) {
+    const uint32_t q = qb + tid;
+    const uint32_t i0 = q * UPD_Q;
+    const bool full = q < nq && i0 + UPD_Q <= a.N;
+    float V[UPD_Q], Iex[UPD_Q], Iin[UPD_Q], in_ex[UPD_Q], in_in[UPD_Q];
+    uint32_t refr[UPD_Q], pi[UPD_Q], gid[UPD_Q];
+    bool live[UPD_Q], spike[UPD_Q];
+    // phase 1: every load of the four neurons (I_in is identically 0 with a merged ring)
+    if (full) {
+      const float4 v = reinterpret_cast<const float4*>(a.V)[q];
+      const float4 e = reinterpret_cast<const float4*>(a.Iex)[q];
+      const float4 x = reinterpret_cast<const float4*>(rex)[q];
+      const uint2 r = reinterpret_cast<const uint2*>(a.refr)[q];
+      const uint2 p = reinterpret_cast<const uint2*>(a.pop_of)[q];
+      V[0] = v.x; V[1] = v.y; V[2] = v.z; V[3] = v.w;
+      Iex[0] = e.x; Iex[1] = e.y; Iex[2] = e.z; Iex[3] = e.w;
+      in_ex[0] = x.x; in_ex[1] = x.y; in_ex[2] = x.z; in_ex[3] = x.w;
+      refr[0] = r.x & 0xFFFFu; refr[1] = r.x >> 16; refr[2] = r.y & 0xFFFFu; refr[3] = r.y >> 16;
+      pi[0] = p.x & 0xFFFFu; pi[1] = p.x >> 16; pi[2] = p.y & 0xFFFFu; pi[3] = p.y >> 16;
+      if (two) {
+        const float4 ii = reinterpret_cast<const float4*>(a.Iin)[q];
+        const float4 y = reinterpret_cast<const float4*>(rin)[q];
+        Iin[0] = ii.x; Iin[1] = ii.y; Iin[2] = ii.z; Iin[3] = ii.w;
+        in_in[0] = y.x; in_in[1] = y.y; in_in[2] = y.z; in_in[3] = y.w;
+      } else {
 #pragma unroll
-    for (int k = 0; k < UPD_ILP; ++k) {
-      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
-      live[k] = i < a.N;
-      if (live[k]) {
-        V[k] = a.V[i]; Iex[k] = a.Iex[i];
-        Iin[k] = a.n_rec == 2 ? a.Iin[i] : 0.f;
-        refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
-        in_ex[k] = rex[i];
-        in_in[k] = a.n_rec == 2 ? rin[i] : 0.f;
-        gid[k] = a.R == 1 ? (uint32_t)i : a.gid_of[i];
+        for (int k = 0; k < UPD_Q; ++k) Iin[k] = in_in[k] = 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) live[k] = true;
+    } else {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        const uint32_t i = i0 + k;
+        live[k] = q < nq && i < a.N;
+        V[k] = Iex[k] = Iin[k] = in_ex[k] = in_in[k] = 0.f;
+        refr[k] = pi[k] = 0;
+        if (live[k]) {
+          V[k] = a.V[i]; Iex[k] = a.Iex[i];
+          refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
+          in_ex[k] = rex[i];
+          if (two) { Iin[k] = a.Iin[i]; in_in[k] = rin[i]; }
+        }
       }
     }
-    // phase 2: propagate state and synaptic input (independent chains)
-    float thr[UPD_ILP], vre[UPD_ILP];
-    uint32_t rst[UPD_ILP];
 #pragma unroll
-    for (int k = 0; k < UPD_ILP; ++k) {
+    for (int k = 0; k < UPD_Q; ++k) gid[k] = a.R == 1 ? i0 + k : (live[k] ? a.gid_of[i0 + k] : 0u);
+    // phase 2: propagate state and synaptic input (independent chains)
+    float thr[UPD_Q], vre[UPD_Q];
+    uint32_t rst[UPD_Q];
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) {
+      thr[k] = 0.f; vre[k] = 0.f; rst[k] = 0;
       if (live[k]) {
         const DevPop P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
         float v = V[k], ie = Iex[k], ii = Iin[k];
@@ -92,19 +127,33 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
         thr[k] = P.Vth; vre[k] = P.Vreset; rst[k] = P.ref_steps;
       }
     }
-    // Poisson drives, in drive order: the neurons' draws are issued together and one
-    // pass over the (ascending) count thresholds serves all of them
-    for (uint32_t q = 0; q < a.ndrives; ++q) {
-      const DevDrive dr = q < MAX_SMEM_DRIVES ? s_dr[q] : a.drives[q];
-      uint32_t wd[UPD_ILP], cnt[UPD_ILP];
-      bool in[UPD_ILP];
+    // Poisson drives, in drive order; one pass over the ascending count thresholds
+    // serves all four neurons
+    for (uint32_t dq = 0; dq < a.ndrives; ++dq) {
+      const DevDrive dr = dq < MAX_SMEM_DRIVES ? s_dr[dq] : a.drives[dq];
+      uint32_t wd[UPD_Q], cnt[UPD_Q];
+      bool in[UPD_Q];
+      if (a.R == 1 && full) {
+        const uint4 b = philox_stream((uint64_t)q | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
+        wd[0] = b.x; wd[1] = b.y; wd[2] = b.z; wd[3] = b.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < UPD_Q; ++k) {
+          wd[k] = 0u;
+          if (live[k]) {
+            const uint4 b = philox_stream((uint64_t)(gid[k] >> 2) | ((uint64_t)n << 32), dr.idx,
+                                          kPurposePoisson, dr.seed);
+            const uint32_t lo = (gid[k] & 1u) ? b.y : b.x, hi = (gid[k] & 1u) ? b.w : b.z;
+            wd[k] = (gid[k] & 2u) ? hi : lo;
+          }
+        }
+      }
       uint32_t wmax = 0;
 #pragma unroll
-      for (int k = 0; k < UPD_ILP; ++k) {
+      for (int k = 0; k < UPD_Q; ++k) {
         in[k] = live[k] && gid[k] - dr.first < dr.n;
-        wd[k] = in[k] ? philox_stream((uint64_t)gid[k] | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed).x : 0u;
         cnt[k] = 0;
-        wmax = wd[k] > wmax ? wd[k] : wmax;
+        if (in[k]) wmax = wd[k] > wmax ? wd[k] : wmax;
       }
       const uint32_t* tb = s_tbl + dr.tbl_off;
       if (dr.tbl_len <= 32) {
@@ -112,21 +161,21 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
           const uint32_t t = tb[j];
           if (t > wmax) break;
 #pragma unroll
-          for (int k = 0; k < UPD_ILP; ++k) cnt[k] += t <= wd[k] ? 1u : 0u;
+          for (int k = 0; k < UPD_Q; ++k) cnt[k] += t <= wd[k] ? 1u : 0u;
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < UPD_ILP; ++k) cnt[k] = upper_bound_u32(tb, dr.tbl_len, wd[k]);
+        for (int k = 0; k < UPD_Q; ++k) cnt[k] = upper_bound_u32(tb, dr.tbl_len, wd[k]);
       }
 #pragma unroll
-      for (int k = 0; k < UPD_ILP; ++k) {
+      for (int k = 0; k < UPD_Q; ++k) {
         if (!in[k]) continue;
-        if (dr.weight >= 0.f || a.n_rec == 1) Iex[k] += (float)cnt[k] * dr.weight;
+        if (dr.weight >= 0.f || !two) Iex[k] += (float)cnt[k] * dr.weight;
         else Iin[k] += (float)cnt[k] * dr.weight;
       }
     }
 #pragma unroll
-    for (int k = 0; k < UPD_ILP; ++k) {
+    for (int k = 0; k < UPD_Q; ++k) {
       spike[k] = false;
       if (live[k] && V[k] >= thr[k]) {
         V[k] = vre[k];
@@ -135,23 +184,31 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
       }
     }
     // phase 3: stores, ring slot cleared, spikes appended
+    if (full) {
+      reinterpret_cast<float4*>(a.V)[q] = make_float4(V[0], V[1], V[2], V[3]);
+      reinterpret_cast<float4*>(a.Iex)[q] = make_float4(Iex[0], Iex[1], Iex[2], Iex[3]);
+      reinterpret_cast<uint2*>(a.refr)[q] = make_uint2(refr[0] | (refr[1] << 16), refr[2] | (refr[3] << 16));
+      reinterpret_cast<float4*>(rex)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (two) {
+        reinterpret_cast<float4*>(a.Iin)[q] = make_float4(Iin[0], Iin[1], Iin[2], Iin[3]);
+        reinterpret_cast<float4*>(rin)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < UPD_ILP; ++k) {
-      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
-      if (i < a.N) {
+      for (int k = 0; k < UPD_Q; ++k) {
+        if (!live[k]) continue;
+        const uint32_t i = i0 + k;
         a.V[i] = V[k];
         a.Iex[i] = Iex[k];
-        if (a.n_rec == 2) a.Iin[i] = Iin[k];
         a.refr[i] = (uint16_t)refr[k];
         rex[i] = 0.f;
-        if (a.n_rec == 2) rin[i] = 0.f;
+        if (two) { a.Iin[i] = Iin[k]; rin[i] = 0.f; }
       }
     }
 #pragma unroll
-    for (int k = 0; k < UPD_ILP; ++k) {
+    for (int k = 0; k < UPD_Q; ++k) {
       // warp-aggregated append of the step's spiking positions (on one rank these are
       // directly the rows to deliver; with several ranks the router expands them)
-      const uint64_t i = base + (uint64_t)k * UPD_BLOCK + tid;
       const uint32_t mask = __ballot_sync(0xffffffffu, spike[k]);
       if (mask) {
         const int leader = __ffs(mask) - 1;
@@ -163,7 +220,7 @@ __global__ void __launch_bounds__(UPD_BLOCK) update_kernel(SimArgs a, uint32_t k
         sbase = __shfl_sync(0xffffffffu, sbase, leader);
         const uint32_t off = __popc(mask & ((1u << lane) - 1));
         if (spike[k]) {
-          a.spk[(uint64_t)(n & 1) * a.N + sbase + off] = (uint32_t)i;
+          a.spk[(uint64_t)(n & 1) * a.N + sbase + off] = i0 + k;
           if (a.log_cap) {
             unsigned long long lb = 0;
             if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
@@ -268,7 +325,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
         if (e < hi && tt[k] < a.N) {
           const uint32_t slot = (n + dd[k]) & a.ring_mask;
           const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
-          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.N + tt[k], ww[k], pol_ring);
+          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
         }
       }
     }
@@ -290,7 +347,7 @@ __global__ void init_state_kernel(SimArgs a, const float* v0) {
 }
 
 cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
-  const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_ILP - 1) / (UPD_BLOCK * UPD_ILP);
+  const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_Q - 1) / (UPD_BLOCK * UPD_Q);
   const unsigned grid = (unsigned)(need < a.update_grid ? need : a.update_grid);
   update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a, k_step);
   return cudaGetLastError();

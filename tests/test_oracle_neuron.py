@@ -95,3 +95,29 @@ def test_stored_fp32_propagators_round_once():
     for k in ["P22", "P20", "P11_ex", "P21_ex"]:
         assert b.c[k][0] == float(np.float32(a.c[k][0]))
         assert abs(b.c[k][0] - a.c[k][0]) <= 2 ** -24 * abs(a.c[k][0])
+
+
+def test_poisson_drive_counts_distribution_and_independence():
+    """Drive counts (four neurons per Philox block): the count histogram over 40,000
+    neuron-steps matches Poisson(nu h) by chi-square, and neighbours that share a block
+    (g, g + 1 with g mod 4 = 0) are uncorrelated, as are blocks of consecutive steps."""
+    from scipy import stats
+    from oracle import sampling as sm
+    lam = 20000.0 * 0.1e-3
+    thr = sm.poisson_table(20000.0, 0.1)
+    n_neurons, steps = 4000, 10
+    counts = np.stack([on.poisson_counts(thr, 0, 1234, 0, n_neurons, n) for n in range(steps)])
+    flat = counts.ravel()
+    assert abs(flat.mean() - lam) < 4 * math.sqrt(lam / flat.size)
+    kmax = 7
+    obs = np.array([np.count_nonzero(flat == k) for k in range(kmax)] + [np.count_nonzero(flat >= kmax)])
+    p = np.array([stats.poisson.pmf(k, lam) for k in range(kmax)] + [stats.poisson.sf(kmax - 1, lam)])
+    chi2 = float(np.sum((obs - flat.size * p) ** 2 / (flat.size * p)))
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3
+    for lane in (1, 2, 3):                      # words of one block
+        r = np.corrcoef(counts[:, 0::4].ravel(), counts[:, lane::4].ravel())[0, 1]
+        assert abs(r) < 4 / math.sqrt(counts[:, 0::4].size)
+    r = np.corrcoef(counts[:-1].ravel(), counts[1:].ravel())[0, 1]   # step n vs n + 1
+    assert abs(r) < 4 / math.sqrt(counts[:-1].size)
+    # a drive over a sub-range draws the same counts as over the whole range
+    np.testing.assert_array_equal(on.poisson_counts(thr, 0, 1234, 1001, 57, 3), counts[3, 1001:1058])
