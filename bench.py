@@ -111,19 +111,29 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of full-size one-pass
+# ncu captures of the timed step, divided by the units the launches processed), with the
+# source file and its sha256[:16] at capture time; profiles/traffic_balanced_500k.md
+# gives the commands and the raw figures.
+TRAFFIC = {
+    "deliver_kernel": {"bytes_per_unit": 23.37, "source": "sim.cu", "source_sha": "eb4a219ce48d7d23"},
+    "update_kernel": {"bytes_per_unit": 16.06, "source": "sim.cu", "source_sha": "eb4a219ce48d7d23"},
+    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "c11accd52487ba79"},
+    "onesweep_pass": {"bytes_per_unit": 16.41, "source": "build.cu", "source_sha": "c11accd52487ba79"},
+    "finalize_kernel": {"bytes_per_unit": 17.08, "source": "build.cu", "source_sha": "c11accd52487ba79"},
+}
+
+
 def traffic_of(kernel: str, units_per_launch: float):
-    """DRAM bytes per launch from the committed ncu summary, when it was taken on the
-    current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
-    d = json.load(open(p)).get(kernel)
+    """Measured DRAM bytes per launch, when the figure was taken on the current kernel
+    source; else None."""
+    d = TRAFFIC.get(kernel)
     if not d:
         return None
     src = os.path.join(ROOT, "paper_2512_09502_gb300", "csrc", d["source"])
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
         return None
-    return d["dram_bytes_per_unit"] * units_per_launch
+    return d["bytes_per_unit"] * units_per_launch
 
 
 def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000):
@@ -248,9 +258,11 @@ def run_ours(args):
         clk.start()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
+        torch.cuda.nvtx.range_push(f"timed_{fmt}")     # lets a profiler select the timed steps
         stats = []
         for _ in range(args.steps):
             stats.append(one(fmt, args.sim_steps)[1])
+        torch.cuda.nvtx.range_pop()
         t1.record(stream)
         barrier()
         clocks = clk.stop()
@@ -315,7 +327,8 @@ def run_ours(args):
         gbps = v["units"] * v["bpu"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None
         table[k] = {"ms_per_launch": v["ms"], "launches_per_step": v["launches"],
                     "share_of_step": v["ms"] * v["launches"] / step_ms, "algorithmic_GBps": gbps,
-                    "frac_of_hbm": gbps / peak if gbps else None}
+                    "frac_of_hbm": gbps / peak if gbps else None,
+                    "traffic_bytes_per_launch": traffic_of(k, v["units"])}
     dom = max((k for k in kern if kern[k]["bound"] == "hbm"), key=lambda k: table[k]["share_of_step"])
     d = kern[dom]
     alg = d["units"] * d["bpu"]
