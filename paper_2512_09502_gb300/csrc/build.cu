@@ -304,9 +304,10 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
     rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
   // Stable warp-level ranking: item j's peers (lanes holding the same digit) come from
-  // one ballot per digit bit, plus one for the out-of-range marker; the leader of each
-  // peer group advances the warp's running count of that digit.
+  // one ballot per digit bit, plus one for the out-of-range marker in a partial tile;
+  // the leader of each peer group advances the warp's running count of that digit.
   const uint32_t lt = (1u << lane) - 1;
+  const int nbits = n == (uint32_t)TILE ? RB : RB + 1;   // the marker bit only in a partial tile
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
@@ -314,9 +315,10 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
     uint32_t peers = 0xffffffffu;
 #pragma unroll
     for (int bit = 0; bit <= RB; ++bit) {
-      const bool set = (d >> bit) & 1u;
-      const uint32_t bl = __ballot_sync(0xffffffffu, set);
-      peers &= set ? bl : ~bl;
+      if (bit == RB && nbits == RB) break;
+      const uint32_t m = 0u - ((d >> bit) & 1u);
+      const uint32_t bl = __ballot_sync(0xffffffffu, m != 0u);
+      peers &= ~(bl ^ m);
     }
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
