@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
   for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
   if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;   // next step's list
-  __syncthreads();
   const uint32_t slot = n & a.ring_mask;
   float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.ring_stride;
   float* rin = rex + a.ring_stride;
   const bool two = a.n_rec == 2;
   const uint32_t nq = (a.N + UPD_Q - 1) / UPD_Q;
+  bool staged = false;             // the shared tables are published by the first iteration's barrier
   for (uint32_t qb = blockIdx.x * UPD_BLOCK; qb < nq; qb += gridDim.x * UPD_BLOCK) {
     const uint32_t q = qb + tid;
     const uint32_t i0 = q * UPD_Q;
@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
     }
 #pragma unroll
     for (int k = 0; k < UPD_Q; ++k) gid[k] = a.R == 1 ? i0 + k : (live[k] ? a.gid_of[i0 + k] : 0u);
+    if (!staged) {                 // block-uniform: the state loads above are already in flight
+      __syncthreads();
+      staged = true;
+    }
     // phase 2: propagate state and synaptic input (independent chains)
     float thr[UPD_Q], vre[UPD_Q];
     uint32_t rst[UPD_Q];
