@@ -304,8 +304,9 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
     rec[j] = idx < n ? in[base + idx] : ~0ull;
   }
   // Stable warp-level ranking: item j's peers (lanes holding the same digit) come from
-  // one ballot per digit bit, plus one for the out-of-range marker in a partial tile;
-  // the leader of each peer group advances the warp's running count of that digit.
+  // one ballot per digit bit, plus one for the out-of-range marker in a partial tile
+  // (or from match.any for every fourth item); the leader of each peer group advances
+  // the warp's running count of that digit.
   const uint32_t lt = (1u << lane) - 1;
   const int nbits = n == (uint32_t)TILE ? RB : RB + 1;   // the marker bit only in a partial tile
 #pragma unroll
@@ -313,12 +314,18 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
     const uint32_t idx = wbase + j * 32 + lane;
     const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
     uint32_t peers = 0xffffffffu;
+    if ((j & 3) == 3) {
+      // every fourth item on the match unit, the rest on ballots: the ballot loop keeps
+      // the ALU pipe busy, and match.any runs beside it
+      peers = __match_any_sync(0xffffffffu, d);
+    } else {
 #pragma unroll
-    for (int bit = 0; bit <= RB; ++bit) {
-      if (bit == RB && nbits == RB) break;
-      const uint32_t m = 0u - ((d >> bit) & 1u);
-      const uint32_t bl = __ballot_sync(0xffffffffu, m != 0u);
-      peers &= ~(bl ^ m);
+      for (int bit = 0; bit <= RB; ++bit) {
+        if (bit == RB && nbits == RB) break;
+        const uint32_t m = 0u - ((d >> bit) & 1u);
+        const uint32_t bl = __ballot_sync(0xffffffffu, m != 0u);
+        peers &= ~(bl ^ m);
+      }
     }
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
