@@ -1119,6 +1119,7 @@ cudaStream_t ctx_stream(snn_ctx* c) { return c->st; }
 MapsState& ctx_maps(snn_ctx* c) { return c->maps; }
 SimArgs& ctx_sim(snn_ctx* c) { return c->sim; }
 const Geom& ctx_geom(snn_ctx* c) { return c->g; }
+uint64_t ctx_geom_synapses(snn_ctx* c) { return c->E; }
 const std::vector<uint64_t>& ctx_seg_start(snn_ctx* c) { return c->seg_start; }
 const std::vector<uint32_t>& ctx_rank_sizes(snn_ctx* c) { return c->M; }
 const std::vector<uint32_t>& ctx_rank_off(snn_ctx* c) { return c->rank_off; }

@@ -461,13 +461,19 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
 
 // ---- routing: spikes -> delivery work items (global rows) ----
 namespace {
+// One warp per spike: the warp reserves the spike's rows in the work list with one
+// atomic, then its lanes fill them in parallel, each row with the rank it belongs to.
 __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
   const uint32_t n = *r.step + k_step;
   const uint32_t nspk = r.n_spk[n & 1];
   const uint32_t* spk = r.spk + (uint64_t)(n & 1) * r.N;
   if (blockIdx.x == 0 && threadIdx.x == 0) r.n_work[(n + 1) & 1] = 0;
   uint32_t* work = r.work + (uint64_t)(n & 1) * r.work_cap;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nspk; k += gridDim.x * blockDim.x) {
+  uint32_t* wtau = r.work_tau + (uint64_t)(n & 1) * r.work_cap;
+  const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k = gw; k < nspk; k += nw) {
     const uint32_t i = spk[k];                               // neuron position
     uint32_t lo = 0, hi = r.R;
     while (lo < hi) {
@@ -475,9 +481,9 @@ __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
       if (r.rank_off[mid] <= i) lo = mid + 1; else hi = mid;
     }
     const uint32_t sig = lo - 1, s = i - r.rank_off[sig];
-    // local row on the source's own rank
-    uint32_t cnt = 1;
+    // rows: the local row on the source's own rank, then one image row per other rank
     uint64_t o0, o1;
+    uint32_t cnt = 1;
     if (r.exchange == 0) {
       o0 = r.tp_ptr[i];
       o1 = r.tp_ptr[i + 1];
@@ -486,30 +492,47 @@ __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
       o0 = r.h_pos[i];
       o1 = r.h_pos[i + 1];
       if (o1 > o0)
-        for (uint32_t tau = 0; tau < r.R; ++tau) cnt += (tau != sig && r.I[o0 * r.R + tau] >= 0) ? 1u : 0u;
+        for (uint32_t t0 = 0; t0 < r.R; t0 += 32) {
+          const uint32_t tau = t0 + lane;
+          const bool has = tau < r.R && tau != sig && r.I[o0 * r.R + tau] >= 0;
+          cnt += __popc(__ballot_sync(0xffffffffu, has));
+        }
     }
-    const uint32_t base = atomicAdd(&r.n_work[n & 1], cnt);
-    if (base + cnt > r.work_cap) {
-      atomicOr(r.err, kErrBounds);
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&r.n_work[n & 1], cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((uint64_t)base + cnt > r.work_cap) {
+      if (lane == 0) atomicOr(r.err, kErrBounds);
       continue;
     }
-    uint32_t w = base;
-    work[w++] = (uint32_t)(r.rows_off[sig] + s);
+    if (lane == 0) {
+      work[base] = (uint32_t)(r.rows_off[sig] + s);
+      wtau[base] = sig;
+    }
     if (r.exchange == 0) {
       // point-to-point: packets of positions P to ranks T, received through L
-      for (uint64_t j = o0; j < o1; ++j) {
+      for (uint64_t j = o0 + lane; j < o1; j += 32) {
         const uint32_t tau = r.T[j];
         const uint32_t slot = sig < tau ? sig + 1 : sig;
         const uint64_t img = r.img_off[(uint64_t)tau * (r.R + 1) + slot] + r.P[j];   // L - M_tau
-        work[w++] = (uint32_t)(r.rows_off[tau] + r.M[tau] + img);
+        const uint64_t wpos = base + 1 + (j - o0);
+        work[wpos] = (uint32_t)(r.rows_off[tau] + r.M[tau] + img);
+        wtau[wpos] = tau;
       }
     } else if (o1 > o0) {
       // collective: position q in H_{0,sigma}, every other rank looks up I
       const uint64_t q = o0;
-      for (uint32_t tau = 0; tau < r.R; ++tau) {
-        if (tau == sig) continue;
-        const int32_t L = r.I[q * r.R + tau];
-        if (L >= 0) work[w++] = (uint32_t)(r.rows_off[tau] + (uint32_t)L);
+      uint32_t w = base + 1;
+      for (uint32_t t0 = 0; t0 < r.R; t0 += 32) {
+        const uint32_t tau = t0 + lane;
+        const int32_t L = (tau < r.R && tau != sig) ? r.I[q * r.R + tau] : -1;
+        const uint32_t m = __ballot_sync(0xffffffffu, L >= 0);
+        if (L >= 0) {
+          const uint32_t wpos = w + __popc(m & lt);
+          work[wpos] = (uint32_t)(r.rows_off[tau] + (uint32_t)L);
+          wtau[wpos] = tau;
+        }
+        w += __popc(m);
       }
     }
   }
@@ -539,11 +562,21 @@ int setup_routing(snn_ctx* c) {
   }
   r.work_cap = std::min<uint64_t>((uint64_t)m.N * maxfan, 0xFFFFFFFFull);
   r.work = alloc_n<uint32_t>(c, 2 * r.work_cap);
+  r.work_tau = alloc_n<uint32_t>(c, 2 * r.work_cap);
   r.n_work = alloc_n<uint32_t>(c, 2);
-  if (!r.work || !r.n_work) return ctx_fail(c, SNN_ENOMEM, "routing: allocation failed");
+  if (!r.work || !r.work_tau || !r.n_work) return ctx_fail(c, SNN_ENOMEM, "routing: allocation failed");
   MCK(cudaMemsetAsync(r.n_work, 0, 8, ctx_stream(c)));
-  s.work = r.work; s.n_work = r.n_work; s.work_stride = r.work_cap;
+  s.work = r.work; s.n_work = r.n_work; s.work_stride = r.work_cap; s.work_rank = r.work_tau;
   s.rows = m.rows; s.rows_off = m.d_rows_off; s.rank_off = m.d_rank_off;
+  // rows average E / (local rows + images); short rows are delivered by lane groups
+  const uint64_t n_rows = m.rows_off.empty() ? 0 : m.rows_off.back();
+  const double avg = n_rows ? (double)ctx_geom_synapses(c) / (double)n_rows : 0.0;
+  s.item_lanes = 0;
+  if (avg < 256.0) {
+    uint32_t L = 4;
+    while (L < 32 && L * 4 < avg) L *= 2;     // about four events per lane
+    s.item_lanes = L;
+  }
   return SNN_OK;
 }
 

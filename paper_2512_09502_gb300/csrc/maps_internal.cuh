@@ -16,7 +16,7 @@ struct RouteArgs {
   const uint64_t* h_pos; const int32_t* I;
   const uint32_t* step; uint32_t* err;
   const uint32_t* spk; const uint32_t* n_spk;
-  uint32_t* work; uint32_t* n_work; uint64_t work_cap;
+  uint32_t* work; uint32_t* work_tau; uint32_t* n_work; uint64_t work_cap;
 };
 
 struct MapsState {
@@ -48,6 +48,7 @@ cudaStream_t ctx_stream(snn_ctx* c);
 MapsState& ctx_maps(snn_ctx* c);
 SimArgs& ctx_sim(snn_ctx* c);
 const Geom& ctx_geom(snn_ctx* c);
+uint64_t ctx_geom_synapses(snn_ctx* c);   // synapses over all ranks
 const std::vector<uint64_t>& ctx_seg_start(snn_ctx* c);
 const std::vector<uint32_t>& ctx_rank_sizes(snn_ctx* c);
 const std::vector<uint32_t>& ctx_rank_off(snn_ctx* c);

@@ -285,15 +285,54 @@ __device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e, uin
   return __half2float(__ushort_as_half((unsigned short)ld_stream_u16(w + e, pol)));
 }
 
+// Events lo + first, lo + first + stride, ... < hi of one row: DEL_ILP events per thread
+// are loaded before their reductions are issued.
+template <typename WT, int STRIDE>
+__device__ __forceinline__ void deliver_span(const SimArgs& a, const WT* __restrict__ w, uint32_t n,
+                                             uint64_t lo, uint64_t hi, uint32_t first, uint32_t stride,
+                                             uint32_t toff, float sc, uint64_t pol_stream, uint64_t pol_ring) {
+  float* __restrict__ ring = a.ring;
+  const uint32_t st = STRIDE ? (uint32_t)STRIDE : stride;
+  for (uint64_t e0 = lo + first; e0 < hi; e0 += (uint64_t)DEL_ILP * st) {
+    float ww[DEL_ILP];
+    uint32_t tt[DEL_ILP], dd[DEL_ILP];
+#pragma unroll
+    for (int k = 0; k < DEL_ILP; ++k) {
+      const uint64_t e = e0 + (uint64_t)k * st;
+      if (e < hi) {
+        ww[k] = load_w<WT>(w, e, pol_stream) * sc;
+        tt[k] = ld_stream_u32(a.tgt + e, pol_stream) + toff;
+        dd[k] = ld_stream_u8(a.d + e, pol_stream);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DEL_ILP; ++k) {
+      const uint64_t e = e0 + (uint64_t)k * st;
+      if (e < hi && tt[k] < a.N) {
+        const uint32_t slot = (n + dd[k]) & a.ring_mask;
+        const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
+        red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void add_events(const SimArgs& a, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.n_events, v);
+}
+
+// Long rows (one rank: full out-degrees): each (row, slice) item is one CTA's work.
 template <typename WT>
 __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT* __restrict__ w,
                                                             uint32_t k_step) {
   const uint32_t n = *a.step + k_step;
   const uint32_t nitems = a.n_work[n & 1];
   const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
+  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)(n & 1) * a.work_stride : nullptr;
   const uint32_t slices = a.slices;
   const uint64_t total = (uint64_t)nitems * slices;
-  float* __restrict__ ring = a.ring;
   const uint64_t pol_stream = policy_evict_first(), pol_ring = policy_evict_last();
   for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
     const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
@@ -302,39 +341,43 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
     const uint64_t len = rb - ra;
     const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
     const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
-    uint32_t toff = 0;                     // first neuron position of the row's rank
-    if (a.R > 1) {
-      uint32_t l = 0, h = a.R;
-      while (l < h) {
-        const uint32_t mid = (l + h) >> 1;
-        if (a.rows_off[mid] <= row) l = mid + 1; else h = mid;
-      }
-      toff = a.rank_off[l - 1];
-    }
-    for (uint64_t e0 = lo + threadIdx.x; e0 < hi; e0 += (uint64_t)DEL_ILP * DEL_BLOCK) {
-      float ww[DEL_ILP];
-      uint32_t tt[DEL_ILP], dd[DEL_ILP];
-#pragma unroll
-      for (int k = 0; k < DEL_ILP; ++k) {
-        const uint64_t e = e0 + (uint64_t)k * DEL_BLOCK;
-        if (e < hi) {
-          ww[k] = load_w<WT>(w, e, pol_stream) * sc;
-          tt[k] = ld_stream_u32(a.tgt + e, pol_stream) + toff;
-          dd[k] = ld_stream_u8(a.d + e, pol_stream);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < DEL_ILP; ++k) {
-        const uint64_t e = e0 + (uint64_t)k * DEL_BLOCK;
-        if (e < hi && tt[k] < a.N) {
-          const uint32_t slot = (n + dd[k]) & a.ring_mask;
-          const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
-          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
-        }
-      }
-    }
-    if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);
+    const uint32_t toff = taus ? a.rank_off[taus[si]] : 0u;   // first neuron position of the row's rank
+    deliver_span<WT, DEL_BLOCK>(a, w, n, lo, hi, threadIdx.x, DEL_BLOCK, toff, sc, pol_stream, pol_ring);
+    if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);   // a few per CTA
   }
+}
+
+// Short rows (many logical ranks: a spike's connections are split into one image row
+// per rank): a group of item_lanes lanes per row, 32 / item_lanes rows per warp in flight.
+template <typename WT>
+__global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, const WT* __restrict__ w,
+                                                                 uint32_t k_step) {
+  const uint32_t n = *a.step + k_step;
+  const uint32_t nitems = a.n_work[n & 1];
+  const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
+  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)(n & 1) * a.work_stride : nullptr;
+  const uint32_t L = a.item_lanes;                     // 4, 8, 16 or 32
+  const uint32_t lane = threadIdx.x & 31, sub = lane / L, sl = lane % L, per_warp = 32 / L;
+  const uint64_t gw = ((uint64_t)blockIdx.x * DEL_BLOCK + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * DEL_BLOCK) >> 5;
+  const uint64_t pol_stream = policy_evict_first(), pol_ring = policy_evict_last();
+  unsigned long long events = 0;
+  for (uint64_t b = gw * per_warp; b < nitems; b += nw * per_warp) {
+    const uint64_t it = b + sub;
+    uint64_t lo = 0, hi = 0;
+    uint32_t toff = 0;
+    float sc = 1.0f;
+    if (it < nitems) {
+      const uint32_t row = items[it];
+      lo = a.rows[row];
+      hi = a.rows[row + 1];
+      toff = taus ? a.rank_off[taus[it]] : 0u;
+      if (a.row_scale) sc = a.row_scale[row];
+      if (sl == 0) events += hi - lo;
+    }
+    deliver_span<WT, 0>(a, w, n, lo, hi, sl, L, toff, sc, pol_stream, pol_ring);
+  }
+  add_events(a, events);
 }
 
 __global__ void advance_step_kernel(uint32_t* step, uint32_t by) { *step += by; }
@@ -357,14 +400,17 @@ cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
+template <typename WT>
+static void launch_deliver_t(const SimArgs& a, const WT* w, uint32_t k_step, cudaStream_t st) {
   const unsigned grid = (unsigned)a.deliver_grid;
-  if (a.w_format == 0)
-    deliver_kernel<float><<<grid, DEL_BLOCK, 0, st>>>(a, (const float*)a.w, k_step);
-  else if (a.w_format == 1)
-    deliver_kernel<__nv_bfloat16><<<grid, DEL_BLOCK, 0, st>>>(a, (const __nv_bfloat16*)a.w, k_step);
-  else
-    deliver_kernel<__half><<<grid, DEL_BLOCK, 0, st>>>(a, (const __half*)a.w, k_step);
+  if (a.item_lanes) deliver_rows_kernel<WT><<<grid, DEL_BLOCK, 0, st>>>(a, w, k_step);
+  else deliver_kernel<WT><<<grid, DEL_BLOCK, 0, st>>>(a, w, k_step);
+}
+
+cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
+  if (a.w_format == 0) launch_deliver_t(a, (const float*)a.w, k_step, st);
+  else if (a.w_format == 1) launch_deliver_t(a, (const __nv_bfloat16*)a.w, k_step, st);
+  else launch_deliver_t(a, (const __half*)a.w, k_step, st);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,9 @@ struct SimArgs {
   uint32_t* step;                             // device step counter (first step of a batch)
   uint32_t* n_spk; uint32_t* spk;             // [2] counts, [2][N] spiking positions
   uint32_t* n_work; uint32_t* work;           // [2] counts, [2][stride] rows to deliver
+  const uint32_t* work_rank;                  // [2][stride] rank of each row (R > 1) or null
   uint64_t work_stride;
+  uint32_t item_lanes;                        // lanes per row for short rows; 0 = CTA per row slice
   unsigned long long* n_logged; uint2* log; unsigned long long log_cap;
   unsigned long long* n_events; unsigned long long* n_spikes_total;
   const uint64_t* rows;                       // row starts (absolute); one rank: gid rows
