@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs 
   __shared__ uint32_t s_tbl[256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1;
+  const uint32_t nb = 32 - __clz(c.R);        // bits of the values 0 .. R
   for (uint64_t tile = blockIdx.x; tile < c.n_ft_tiles; tile += gridDim.x) {
     __syncthreads();
     for (uint32_t i = tid; i < NW * c.R; i += 256) s_w[i / c.R][i % c.R] = 0;
@@ -578,7 +579,14 @@ __global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs 
         const uint32_t src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
         rec[j] = make_record(P, a.g, rk[j], cc, src, b.y, s_tbl);
       }
-      const uint32_t peers = __match_any_sync(0xffffffffu, rk[j]);
+      // peers (same target rank) from one ballot per bit of the rank (R marks no draw)
+      const uint32_t key = rk[j] == 0xFFFFFFFFu ? c.R : rk[j];
+      uint32_t peers = 0xffffffffu;
+      for (uint32_t bit = 0; bit < nb; ++bit) {
+        const uint32_t m = 0u - ((key >> bit) & 1u);
+        const uint32_t bl = __ballot_sync(0xffffffffu, m != 0u);
+        peers &= ~(bl ^ m);
+      }
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
       if (lane == leader && rk[j] != 0xFFFFFFFFu) {

@@ -190,6 +190,31 @@ __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_
   }
 }
 
+// dst[k] = src[k * stride] (stride > 0) or src[idx[k]] (idx given): boundary values of a
+// scan gathered on the device so that the host reads them in one copy
+__global__ void gather_u64(const uint64_t* src, uint64_t stride, const uint32_t* idx, uint64_t count,
+                           uint64_t* dst) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    dst[k] = src[idx ? (uint64_t)idx[k] : k * stride];
+}
+
+// *out = max over i < n of ptr[i + 1] - ptr[i] (out starts at 0)
+__global__ void max_gap(const uint64_t* ptr, uint64_t n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long g = ptr[i + 1] - ptr[i];
+    m = g > m ? g : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void u8_to_u32(const uint8_t* in, uint64_t n, uint32_t* out) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)
@@ -327,6 +352,20 @@ static T* alloc_n(snn_ctx* c, uint64_t n) {
   return (T*)ctx_alloc(c, std::max<uint64_t>(n, 1) * sizeof(T));
 }
 
+// host copy of src[k * stride] (or src[idx[k]]) for k < count, one device gather and one copy
+static int read_boundaries(snn_ctx* c, const uint64_t* src, uint64_t stride, const uint32_t* idx, uint64_t count,
+                           uint64_t* host) {
+  cudaStream_t st = ctx_stream(c);
+  uint64_t* tmp = alloc_n<uint64_t>(c, count);
+  if (!tmp) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
+  gather_u64<<<grid_for(c, count), MB, 0, st>>>(src, stride, idx, count, tmp);
+  MCK(cudaGetLastError());
+  MCK(cudaMemcpyAsync(host, tmp, count * 8, cudaMemcpyDeviceToHost, st));
+  MCK(cudaStreamSynchronize(st));
+  ctx_free(c, tmp);
+  return SNN_OK;
+}
+
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase) {
   MapsState& m = ctx_maps(c);
   cudaStream_t st = ctx_stream(c);
@@ -355,9 +394,10 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   MCK(exclusive_scan(c, flag, RN, img_pos));
   // images per rank: img_pos at rank boundaries
   std::vector<uint64_t> bounds(R + 1);
-  for (uint32_t t = 0; t <= R; ++t)
-    MCK(cudaMemcpyAsync(&bounds[t], img_pos + (uint64_t)t * N, 8, cudaMemcpyDeviceToHost, st));
-  MCK(cudaStreamSynchronize(st));
+  {
+    const int rc = read_boundaries(c, img_pos, N, nullptr, R + 1, bounds.data());
+    if (rc != SNN_OK) return rc;
+  }
   m.n_img.assign(R, 0);
   m.img_first.assign(R + 1, 0);
   m.rows_off.assign(R + 1, 0);
@@ -410,9 +450,10 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   ctx_free(c, f32v);
   // S offsets per (sigma, tau): positions at plane boundaries
   m.S_off.assign((size_t)R * R + 1, 0);
-  for (uint64_t k = 0; k <= (uint64_t)R * R; ++k)
-    MCK(cudaMemcpyAsync(&m.S_off[k], m.spos + k * Mmax, 8, cudaMemcpyDeviceToHost, st));
-  MCK(cudaStreamSynchronize(st));
+  {
+    const int rc = read_boundaries(c, m.spos, Mmax, nullptr, (uint64_t)R * R + 1, m.S_off.data());
+    if (rc != SNN_OK) return rc;
+  }
   m.d_S_off = alloc_n<uint64_t>(c, (uint64_t)R * R + 1);
   m.S_vals = alloc_n<uint32_t>(c, m.S_off[(size_t)R * R]);
   if (!m.d_S_off || !m.S_vals) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
@@ -433,9 +474,10 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   MCK(cudaMemcpyAsync(&ntp, m.tp_ptr + N, 8, cudaMemcpyDeviceToHost, st));
   MCK(cudaMemcpyAsync(&nh, m.h_pos + N, 8, cudaMemcpyDeviceToHost, st));
   m.h_off.assign(R + 1, 0);
-  for (uint32_t t = 0; t <= R; ++t)
-    MCK(cudaMemcpyAsync(&m.h_off[t], m.h_pos + roff[t], 8, cudaMemcpyDeviceToHost, st));
-  MCK(cudaStreamSynchronize(st));
+  {
+    const int rc = read_boundaries(c, m.h_pos, 0, m.d_rank_off, R + 1, m.h_off.data());
+    if (rc != SNN_OK) return rc;
+  }
   m.n_tp = ntp;
   m.n_h = nh;
   m.T = alloc_n<uint32_t>(c, ntp);
@@ -554,10 +596,16 @@ int setup_routing(snn_ctx* c) {
   uint64_t maxfan = 1 + (r.exchange == 0 ? 0 : (uint64_t)m.R - 1);
   if (r.exchange == 0) {
     // the largest T list
-    std::vector<uint64_t> tp(m.N + 1);
-    MCK(cudaMemcpy(tp.data(), m.tp_ptr, (m.N + 1) * 8, cudaMemcpyDeviceToHost));
-    uint64_t mx = 0;
-    for (uint32_t i = 0; i < m.N; ++i) mx = std::max(mx, tp[i + 1] - tp[i]);
+    unsigned long long* d_mx = alloc_n<unsigned long long>(c, 1);
+    if (!d_mx) return ctx_fail(c, SNN_ENOMEM, "routing: allocation failed");
+    cudaStream_t st = ctx_stream(c);
+    MCK(cudaMemsetAsync(d_mx, 0, 8, st));
+    max_gap<<<grid_for(c, m.N), MB, 0, st>>>(m.tp_ptr, m.N, d_mx);
+    MCK(cudaGetLastError());
+    unsigned long long mx = 0;
+    MCK(cudaMemcpyAsync(&mx, d_mx, 8, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    ctx_free(c, d_mx);
     maxfan = 1 + mx;
   }
   r.work_cap = std::min<uint64_t>((uint64_t)m.N * maxfan, 0xFFFFFFFFull);
