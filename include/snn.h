@@ -103,6 +103,15 @@ typedef struct snn_config {
                                   (no graph then); results in snn_stats_t              */
   int32_t sort_items;          /* records per thread of a sort tile: 8, 12, 16; 0 = tuned */
   int32_t deliver_ctas_per_sm; /* delivery grid = SMs x this (1..32); 0 = tuned          */
+  /* Dry run (Results, "Collective communication": each process builds its regular share
+     of a larger network in the absence of the rest, to estimate memory and construction
+     time): with dry_run = 1 and n_ranks > 1, snn_calibrate builds only the connections,
+     image rows and R/L maps of rank dry_run_rank, as if n_ranks ranks existed.  Fixed
+     in-degree rules only (EINVAL otherwise); no source-side maps and no simulation state:
+     snn_simulate, snn_get_spikes and snn_get_state return ESTATE, snn_get_connections /
+     snn_get_row / snn_get_maps (R, L) answer for that rank only.  0 = off. */
+  int32_t dry_run;
+  uint32_t dry_run_rank;
 } snn_config;
 
 /* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsnn.so")
 
 SNN_OK = 0
+SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_ETIMEOUT, SNN_ESTATE, SNN_EOVERFLOW = -1, -2, -3, -4, -5, -6
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE", -6: "EOVERFLOW"}
 RULES = {"fixed_indegree": 0, "fixed_total": 1, "pairwise_bernoulli": 2}
 W_KINDS = {"const": 0, "normal_sign": 1}
@@ -44,7 +45,8 @@ class snn_config(C.Structure):
     _fields_ = [("dt_ms", C.c_double), ("n_ranks", C.c_uint32), ("weight_format", C.c_int32),
                 ("exchange", C.c_int32), ("use_graph", C.c_int32),
                 ("spike_log_capacity", C.c_uint64), ("radix_bits", C.c_int32), ("device", C.c_int32),
-                ("profile_kernels", C.c_int32), ("sort_items", C.c_int32), ("deliver_ctas_per_sm", C.c_int32)]
+                ("profile_kernels", C.c_int32), ("sort_items", C.c_int32), ("deliver_ctas_per_sm", C.c_int32),
+                ("dry_run", C.c_int32), ("dry_run_rank", C.c_uint32)]
 
 
 class snn_iaf_psc_exp_params(C.Structure):
@@ -163,7 +165,7 @@ class Context:
                  exchange: str = "p2p", use_graph: bool = True, spike_log_capacity: int = 0,
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
                  stream: Optional[int] = None, profile_kernels: bool = False, sort_items: int = 0,
-                 deliver_ctas_per_sm: int = 0):
+                 deliver_ctas_per_sm: int = 0, dry_run_rank: Optional[int] = None):
         self.lib = load()
         if not (radix_bits and sort_items and deliver_ctas_per_sm):
             from . import autotune        # tuned launch parameters, when a cache exists
@@ -173,7 +175,8 @@ class Context:
             deliver_ctas_per_sm = deliver_ctas_per_sm or int(tuned.get("deliver_ctas_per_sm", 0))
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
-                         1 if profile_kernels else 0, sort_items, deliver_ctas_per_sm)
+                         1 if profile_kernels else 0, sort_items, deliver_ctas_per_sm,
+                         0 if dry_run_rank is None else 1, 0 if dry_run_rank is None else dry_run_rank)
         self._allocator = allocator
         h = C.c_void_p()
         rc = self.lib.snn_create(C.byref(cfg), C.byref(allocator.struct) if allocator else None,

@@ -102,6 +102,7 @@ namespace {
 
 int fail(snn_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
+  if (code == SNN_ECUDA) (void)cudaGetLastError();   // a non-sticky error must not leak into later calls
   return code;
 }
 
@@ -282,6 +283,9 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
     const uint32_t it = config->sort_items ? (uint32_t)config->sort_items : 16u;
     if (!sort_config_supported(rb, it)) return SNN_EINVAL;
     if (config->deliver_ctas_per_sm < 0 || config->deliver_ctas_per_sm > 32) return SNN_EINVAL;
+  if (config->dry_run != 0 && (config->dry_run != 1 || config->n_ranks < 2 ||
+                               config->dry_run_rank >= config->n_ranks))
+    return SNN_EINVAL;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
@@ -493,6 +497,11 @@ int snn_calibrate(snn_ctx* c) {
     }
   }
   const bool counted = !ft_proj.empty() || !pb_proj.empty();
+  const bool dry = c->cfg.dry_run != 0;
+  const uint32_t dr = dry ? c->cfg.dry_run_rank : 0;
+  if (dry && counted)
+    return fail(c, SNN_EINVAL, "a dry run supports the fixed in-degree rule only (the other rules are placed "
+                               "by counting draws over every rank)");
   CountedArgs ca{};
   std::vector<uint64_t> ft_tot_h, pb_tot_h;
   std::vector<void*> counted_bufs;
@@ -537,6 +546,7 @@ int snn_calibrate(snn_ctx* c) {
   uint64_t pos = 0, tiles = 0;
   for (uint32_t t = 0; t < R; ++t) {
     c->seg_start[t] = pos;
+    if (dry && t != dr) continue;               // a dry run generates only its rank's targets
     uint32_t kft = 0, kpb = 0;
     for (uint32_t i = 0; i < P; ++i) {
       const ProjSpec& s = c->projs[i];
@@ -662,7 +672,7 @@ int snn_calibrate(snn_ctx* c) {
   c->d_w = dalloc(c, std::max<uint64_t>(E, 1) * c->wbytes);
   if (!c->d_w) return fail(c, SNN_ENOMEM, "allocation failed: weights");
   AL(c->d_d, std::max<uint64_t>(E, 1), "delays");
-  AL(c->d_dense, (uint64_t)R * (N + 1), "row starts");
+  AL(c->d_dense, (uint64_t)(dry ? 1 : R) * (N + 1), "row starts");
   if (c->cfg.weight_format == SNN_WEIGHT_F16) {
     // per source gid: power-of-two scale of the largest |mean| among its projections
     std::vector<float> sc(N, 1.0f);
@@ -682,6 +692,7 @@ int snn_calibrate(snn_ctx* c) {
   }
   a.tgt = c->d_tgt; a.w = c->d_w; a.d = c->d_d; a.w_format = (uint32_t)c->cfg.weight_format;
   a.dense = c->d_dense; a.row_scale_src = c->d_scale_src;
+  a.dense_seg0 = dry ? dr : 0; a.dense_nseg = dry ? 1 : R;
   CK(launch_finalize(a, cur, E, c->st));
   c->stats.kernel_launches += E ? 2 : 1;
   CK(cudaEventRecord(ev[3], c->st));
@@ -692,15 +703,17 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- image neurons and communication maps (logical ranks) ----
   if (R > 1) {
-    int rc = build_maps(c, dp, d_projs, d_cbase);
+    int rc = dry ? build_maps_dry(c, dr) : build_maps(c, dp, d_projs, d_cbase);
     if (rc != SNN_OK) return rc;
   }
   CK(cudaEventRecord(ev[4], c->st));
 
-  // ---- simulation state ----
+  // ---- simulation state (a dry run builds connections only) ----
   uint32_t D = 1;
   while (D < dmax + 1) D <<= 1;
   c->ring_slots = D;
+  float* d_v0 = nullptr;
+  if (!dry) {
   SimArgs& s = c->sim;
   s.N = N; s.R = R;
   AL(s.V, N, "V"); AL(s.Iex, N, "Iex"); AL(s.Iin, N, "Iin"); AL(s.refr, N, "refr");
@@ -723,7 +736,7 @@ int snn_calibrate(snn_ctx* c) {
       v0[ppos] = (float)v;
     }
   }
-  uint16_t* d_pop_of; DevPop* d_pops; float* d_v0;
+  uint16_t* d_pop_of; DevPop* d_pops;
   UP(d_pop_of, pop_of, "population index");
   UP(d_pops, dpops, "populations");
   UP(d_v0, v0, "V0");
@@ -787,9 +800,10 @@ int snn_calibrate(snn_ctx* c) {
   }
   CK(launch_init_state(s, d_v0, c->st));
   c->stats.kernel_launches += 1;
+  }
   CK(cudaEventRecord(ev[5], c->st));
   CK(cudaStreamSynchronize(c->st));
-  dfree(c, d_v0);
+  if (d_v0) dfree(c, d_v0);
   uint32_t herr = 0;
   CK(cudaMemcpy(&herr, c->d_err, 4, cudaMemcpyDeviceToHost));
   c->stats.d2h_bytes += 4;
@@ -878,6 +892,7 @@ static int build_graph(snn_ctx* c, uint32_t steps) {
 int snn_simulate(snn_ctx* c, uint32_t steps) {
   if (!c) return SNN_EINVAL;
   if (!c->calibrated) return fail(c, SNN_ESTATE, "simulate before calibrate");
+  if (c->cfg.dry_run) return fail(c, SNN_ESTATE, "a dry run builds connections only");
   CK(cudaSetDevice(c->cfg.device));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -917,6 +932,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
 int snn_get_spikes(snn_ctx* c, uint32_t* host_step, uint32_t* host_gid, uint64_t cap, uint64_t* n_out) {
   if (!c) return SNN_EINVAL;
   if (!c->calibrated) return fail(c, SNN_ESTATE, "no simulation");
+  if (c->cfg.dry_run) return fail(c, SNN_ESTATE, "a dry run builds connections only");
   unsigned long long n = 0;
   CK(cudaMemcpyAsync(&n, c->sim.n_logged, 8, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -942,6 +958,7 @@ int snn_get_spikes(snn_ctx* c, uint32_t* host_step, uint32_t* host_gid, uint64_t
 int snn_get_state(snn_ctx* c, uint32_t first, uint32_t n, float* V, float* Iex, float* Iin) {
   if (!c) return SNN_EINVAL;
   if (!c->calibrated) return fail(c, SNN_ESTATE, "no state before calibrate");
+  if (c->cfg.dry_run) return fail(c, SNN_ESTATE, "a dry run builds connections only");
   if ((uint64_t)first + n > c->N) return fail(c, SNN_EINVAL, "range beyond neurons");
   const uint32_t N = c->N;
   float* src[3] = {c->sim.V, c->sim.Iex, c->sim.Iin};
@@ -1061,7 +1078,7 @@ int snn_stats(snn_ctx* c, snn_stats_t* out) {
   s.device_bytes = c->cur_bytes;
   s.peak_device_bytes = c->peak_bytes;
   s.n_images = c->maps.n_images_total;
-  if (c->calibrated) {
+  if (c->calibrated && !c->cfg.dry_run) {
     unsigned long long v[2] = {0, 0};
     CK(cudaMemcpy(&v[0], c->sim.n_spikes_total, 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&v[1], c->sim.n_events, 8, cudaMemcpyDeviceToHost));

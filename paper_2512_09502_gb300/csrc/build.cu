@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
     uint32_t seg = g.R == 1 ? 0u : upper_bound_u64(a.seg_start + 1, g.R, i0);
     uint64_t seg_hi = a.seg_start[seg + 1];
     const uint32_t* doff = a.dense_off + (uint64_t)seg * g.R;
-    uint64_t* dn = a.dense + (uint64_t)seg * ((uint64_t)g.N + 1);
+    uint64_t* dn = a.dense + (uint64_t)(seg - a.dense_seg0) * ((uint64_t)g.N + 1);
     int64_t prow = -1;
     if (i0 > a.seg_start[seg]) {
       const uint64_t kp = rec[i0 - 1] >> g.cbits;
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
         ++seg;
         seg_hi = a.seg_start[seg + 1];
         doff = a.dense_off + (uint64_t)seg * g.R;
-        dn = a.dense + (uint64_t)seg * ((uint64_t)g.N + 1);
+        dn = a.dense + (uint64_t)(seg - a.dense_seg0) * ((uint64_t)g.N + 1);
         prow = -1;
       }
       const uint64_t key = r[j] >> g.cbits;
@@ -852,20 +852,21 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
   }
 }
 
-__global__ void fill_empty_segments(uint64_t* dense, const uint64_t* seg_start, uint32_t R,
+__global__ void fill_empty_segments(uint64_t* dense, const uint64_t* seg_start, uint32_t seg0, uint32_t nseg,
                                     uint32_t N) {
-  const uint64_t total = (uint64_t)R * (N + 1);
+  const uint64_t total = (uint64_t)nseg * (N + 1);
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t seg = (uint32_t)(i / (N + 1));
+    const uint32_t seg = seg0 + (uint32_t)(i / (N + 1));
     if (seg_start[seg] == seg_start[seg + 1]) dense[i] = seg_start[seg];
   }
 }
 
 cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E, cudaStream_t st) {
-  const uint64_t total = (uint64_t)a.g.R * (a.g.N + 1);
-  fill_empty_segments<<<(unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)a.num_sms * 16), 256, 0,
-                        st>>>(a.dense, a.seg_start, a.g.R, a.g.N);
+  const uint64_t total = (uint64_t)a.dense_nseg * (a.g.N + 1);
+  if (total)
+    fill_empty_segments<<<(unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)a.num_sms * 16), 256, 0,
+                          st>>>(a.dense, a.seg_start, a.dense_seg0, a.dense_nseg, a.g.N);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || E == 0) return e;
   const uint64_t nq = (E + FIN_Q - 1) / FIN_Q;

@@ -17,6 +17,7 @@
 // ascending order.
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "maps_internal.cuh"
@@ -108,30 +109,33 @@ cudaError_t exclusive_scan(snn_ctx* c, const uint32_t* in, uint64_t n, uint64_t*
 }
 
 // ---- target side: image rows ----
-// used[tau][r] for the dense rows r >= M_tau (image candidates): row has connections
-__global__ void image_flags(const uint64_t* dense, uint32_t N, uint32_t R, const uint32_t* M,
-                            uint32_t* flag /*[R][N]*/) {
-  const uint64_t total = (uint64_t)R * N;
+// Target-side kernels work on a window of ranks tau = t0 + tl, tl < nt, whose dense row
+// starts are dense[tl][N + 1] (the whole network: t0 = 0, nt = R; a dry run: one rank).
+// used[tl][r] for the dense rows r >= M_tau (image candidates): row has connections
+__global__ void image_flags(const uint64_t* dense, uint32_t N, uint32_t t0, uint32_t nt, const uint32_t* M,
+                            uint32_t* flag /*[nt][N]*/) {
+  const uint64_t total = (uint64_t)nt * N;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t tau = (uint32_t)(i / N), r = (uint32_t)(i - (uint64_t)tau * N);
-    const uint64_t* dn = dense + (uint64_t)tau * (N + 1);
-    flag[i] = (r >= M[tau] && dn[r + 1] > dn[r]) ? 1u : 0u;
+    const uint32_t tl = (uint32_t)(i / N), r = (uint32_t)(i - (uint64_t)tl * N);
+    const uint64_t* dn = dense + (uint64_t)tl * (N + 1);
+    flag[i] = (r >= M[t0 + tl] && dn[r + 1] > dn[r]) ? 1u : 0u;
   }
 }
 
-// rows of every rank: local rows, then images; image source (sigma, s)
-__global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, const uint32_t* M,
-                           const uint32_t* flag, const uint64_t* img_pos /*[R*N+1]*/,
-                           const uint64_t* rows_off /*[R+1]*/, const uint32_t* dense_off,
+// rows of every rank of the window: local rows, then images; image source (sigma, s)
+__global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, uint32_t t0, uint32_t nt,
+                           const uint32_t* M, const uint32_t* flag, const uint64_t* img_pos /*[nt*N+1]*/,
+                           const uint64_t* rows_off /*[nt+1]*/, const uint32_t* dense_off,
                            const uint64_t* seg_start, uint64_t* rows, uint32_t* img_gid) {
-  const uint64_t total = (uint64_t)R * N;
+  const uint64_t total = (uint64_t)nt * N;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t tau = (uint32_t)(i / N), r = (uint32_t)(i - (uint64_t)tau * N);
-    const uint64_t* dn = dense + (uint64_t)tau * (N + 1);
-    const uint64_t img_first = img_pos[(uint64_t)tau * N];          // images before rank tau
-    const uint64_t rbase = rows_off[tau];
+    const uint32_t tl = (uint32_t)(i / N), r = (uint32_t)(i - (uint64_t)tl * N);
+    const uint32_t tau = t0 + tl;
+    const uint64_t* dn = dense + (uint64_t)tl * (N + 1);
+    const uint64_t img_first = img_pos[(uint64_t)tl * N];          // images before rank tau
+    const uint64_t rbase = rows_off[tl];
     if (r < M[tau]) {
       rows[rbase + r] = dn[r];
     } else if (flag[i]) {
@@ -148,7 +152,7 @@ __global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, const 
       const uint32_t sig = slot == 0 ? tau : (slot <= tau ? slot - 1 : slot);
       img_gid[img_pos[i]] = (r - doff[slot]) * R + sig;
     }
-    if (r == N - 1) rows[rows_off[tau + 1] - 1] = seg_start[tau + 1];   // terminal entry
+    if (r == N - 1) rows[rows_off[tl + 1] - 1] = seg_start[tau + 1];   // terminal entry
   }
 }
 
@@ -325,14 +329,15 @@ __global__ void img_s_of_gid(const uint32_t* img_gid, uint64_t n, uint32_t R, ui
     img_s[i] = (uint32_t)div_magic(img_gid[i], R, magic_R);
 }
 
-// image counts per (tau, slot) from the image prefix positions
-__global__ void img_slot_offsets(const uint64_t* img_pos, uint32_t N, uint32_t R, const uint32_t* dense_off,
-                                 const uint64_t* img_first, uint64_t* img_off /*[R][R+1]*/) {
+// image counts per (tau, slot) of the window from the image prefix positions
+__global__ void img_slot_offsets(const uint64_t* img_pos, uint32_t N, uint32_t R, uint32_t t0, uint32_t nt,
+                                 const uint32_t* dense_off, const uint64_t* img_first,
+                                 uint64_t* img_off /*[nt][R+1]*/) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= R * (R + 1)) return;
-  const uint32_t tau = k / (R + 1), slot = k - tau * (R + 1);
-  const uint64_t r = slot < R ? dense_off[(uint64_t)tau * R + slot] : N;
-  img_off[k] = img_pos[(uint64_t)tau * N + r] - img_first[tau];
+  if (k >= nt * (R + 1)) return;
+  const uint32_t tl = k / (R + 1), slot = k - tl * (R + 1);
+  const uint64_t r = slot < R ? dense_off[(uint64_t)(t0 + tl) * R + slot] : N;
+  img_off[k] = img_pos[(uint64_t)tl * N + r] - img_first[tl];
 }
 
 unsigned grid_for(snn_ctx* c, uint64_t n) {
@@ -366,7 +371,8 @@ static int read_boundaries(snn_ctx* c, const uint64_t* src, uint64_t stride, con
   return SNN_OK;
 }
 
-int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase) {
+// rank sizes and first positions on the device (both builds)
+static int maps_ranks(snn_ctx* c) {
   MapsState& m = ctx_maps(c);
   cudaStream_t st = ctx_stream(c);
   const Geom& g = ctx_geom(c);
@@ -383,52 +389,78 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   if (!m.d_M || !m.d_rank_off) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
   MCK(cudaMemcpyAsync(m.d_M, Mh.data(), R * 4, cudaMemcpyHostToDevice, st));
   MCK(cudaMemcpyAsync(m.d_rank_off, roff.data(), (R + 1) * 4, cudaMemcpyHostToDevice, st));
+  return SNN_OK;
+}
 
-  // ---- target side: images and per-rank rows ----
-  const uint64_t RN = (uint64_t)R * N;
+// Target side for the ranks t0 .. t0 + nt - 1 (dense row starts [nt][N + 1]): images,
+// per-rank compacted rows (local rows, then images), R/L offsets per (rank, slot).
+static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt) {
+  MapsState& m = ctx_maps(c);
+  cudaStream_t st = ctx_stream(c);
+  const Geom& g = ctx_geom(c);
+  const uint32_t R = g.R, N = g.N;
+  const uint64_t RN = (uint64_t)nt * N;
   uint32_t* flag = alloc_n<uint32_t>(c, RN);
   uint64_t* img_pos = alloc_n<uint64_t>(c, RN + 1);
   if (!flag || !img_pos) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
-  image_flags<<<grid_for(c, RN), MB, 0, st>>>(ctx_dense(c), N, R, m.d_M, flag);
+  image_flags<<<grid_for(c, RN), MB, 0, st>>>(ctx_dense(c), N, t0, nt, m.d_M, flag);
   MCK(cudaGetLastError());
   MCK(exclusive_scan(c, flag, RN, img_pos));
   // images per rank: img_pos at rank boundaries
-  std::vector<uint64_t> bounds(R + 1);
+  std::vector<uint64_t> bounds(nt + 1);
   {
-    const int rc = read_boundaries(c, img_pos, N, nullptr, R + 1, bounds.data());
+    const int rc = read_boundaries(c, img_pos, N, nullptr, nt + 1, bounds.data());
     if (rc != SNN_OK) return rc;
   }
-  m.n_img.assign(R, 0);
-  m.img_first.assign(R + 1, 0);
-  m.rows_off.assign(R + 1, 0);
-  for (uint32_t t = 0; t < R; ++t) {
+  m.t0 = t0;
+  m.nt = nt;
+  m.n_img.assign(nt, 0);
+  m.img_first.assign(nt + 1, 0);
+  m.rows_off.assign(nt + 1, 0);
+  for (uint32_t t = 0; t < nt; ++t) {
     m.n_img[t] = bounds[t + 1] - bounds[t];
     m.img_first[t + 1] = m.img_first[t] + m.n_img[t];
-    m.rows_off[t + 1] = m.rows_off[t] + Mh[t] + m.n_img[t] + 1;
+    m.rows_off[t + 1] = m.rows_off[t] + m.M[t0 + t] + m.n_img[t] + 1;
   }
-  m.n_images_total = m.img_first[R];
-  m.d_rows_off = alloc_n<uint64_t>(c, R + 1);
-  m.d_img_first = alloc_n<uint64_t>(c, R + 1);
-  m.rows = alloc_n<uint64_t>(c, m.rows_off[R]);
+  m.n_images_total = m.img_first[nt];
+  m.d_rows_off = alloc_n<uint64_t>(c, nt + 1);
+  m.d_img_first = alloc_n<uint64_t>(c, nt + 1);
+  m.rows = alloc_n<uint64_t>(c, m.rows_off[nt]);
   m.img_gid = alloc_n<uint32_t>(c, m.n_images_total);
   m.img_s = alloc_n<uint32_t>(c, m.n_images_total);
-  m.d_img_off = alloc_n<uint64_t>(c, (uint64_t)R * (R + 1));
+  m.d_img_off = alloc_n<uint64_t>(c, (uint64_t)nt * (R + 1));
   if (!m.d_rows_off || !m.d_img_first || !m.rows || !m.img_gid || !m.img_s || !m.d_img_off)
     return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
-  MCK(cudaMemcpyAsync(m.d_rows_off, m.rows_off.data(), (R + 1) * 8, cudaMemcpyHostToDevice, st));
-  MCK(cudaMemcpyAsync(m.d_img_first, m.img_first.data(), (R + 1) * 8, cudaMemcpyHostToDevice, st));
-  image_fill<<<grid_for(c, RN), MB, 0, st>>>(ctx_dense(c), N, R, m.d_M, flag, img_pos, m.d_rows_off,
+  MCK(cudaMemcpyAsync(m.d_rows_off, m.rows_off.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, st));
+  MCK(cudaMemcpyAsync(m.d_img_first, m.img_first.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, st));
+  image_fill<<<grid_for(c, RN), MB, 0, st>>>(ctx_dense(c), N, R, t0, nt, m.d_M, flag, img_pos, m.d_rows_off,
                                             ctx_dense_off(c), ctx_dseg_start(c), m.rows, m.img_gid);
   MCK(cudaGetLastError());
-  img_s_of_gid<<<grid_for(c, m.n_images_total), MB, 0, st>>>(m.img_gid, m.n_images_total, R, g.magic_R, m.img_s);
+  if (m.n_images_total)
+    img_s_of_gid<<<grid_for(c, m.n_images_total), MB, 0, st>>>(m.img_gid, m.n_images_total, R, g.magic_R, m.img_s);
   MCK(cudaGetLastError());
-  img_slot_offsets<<<(R * (R + 1) + MB - 1) / MB, MB, 0, st>>>(img_pos, N, R, ctx_dense_off(c), m.d_img_first,
-                                                              m.d_img_off);
+  img_slot_offsets<<<(nt * (R + 1) + MB - 1) / MB, MB, 0, st>>>(img_pos, N, R, t0, nt, ctx_dense_off(c),
+                                                               m.d_img_first, m.d_img_off);
   MCK(cudaGetLastError());
-  m.img_off.resize((size_t)R * (R + 1));
-  MCK(cudaMemcpyAsync(m.img_off.data(), m.d_img_off, (size_t)R * (R + 1) * 8, cudaMemcpyDeviceToHost, st));
+  m.img_off.resize((size_t)nt * (R + 1));
+  MCK(cudaMemcpyAsync(m.img_off.data(), m.d_img_off, (size_t)nt * (R + 1) * 8, cudaMemcpyDeviceToHost, st));
   ctx_free(c, flag);
   ctx_free(c, img_pos);
+
+  return SNN_OK;
+}
+
+int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase) {
+  MapsState& m = ctx_maps(c);
+  cudaStream_t st = ctx_stream(c);
+  const Geom& g = ctx_geom(c);
+  const uint32_t R = g.R, N = g.N;
+  const auto& roff = ctx_rank_off(c);
+  int rc = maps_ranks(c);
+  if (rc != SNN_OK) return rc;
+  const uint32_t Mmax = m.Mmax;
+  rc = maps_target(c, 0, R);
+  if (rc != SNN_OK) return rc;
 
   // ---- source side: regenerated sources -> S, T/P, H, I, G/Q ----
   const uint64_t nf = (uint64_t)R * R * Mmax;
@@ -498,6 +530,18 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   ctx_free(c, inh);
   ctx_free(c, sflag);
   MCK(cudaStreamSynchronize(st));
+  return SNN_OK;
+}
+
+// Dry run (one rank's share of the network): the target side of that rank only; the
+// source-side maps would need every rank's connections.
+int build_maps_dry(snn_ctx* c, uint32_t rank) {
+  int rc = maps_ranks(c);
+  if (rc != SNN_OK) return rc;
+  rc = maps_target(c, rank, 1);
+  if (rc != SNN_OK) return rc;
+  ctx_maps(c).dry = true;
+  MCK(cudaStreamSynchronize(ctx_stream(c)));
   return SNN_OK;
 }
 
@@ -637,6 +681,17 @@ cudaError_t launch_route(snn_ctx* c, uint32_t k_step) {
 uint32_t route_kernels_per_step(snn_ctx* c) { return ctx_geom(c).R > 1 ? 1 : 0; }
 
 // ---- inspection ----
+// index of `rank` in the target-side arrays, or -1 (with the error set) when a dry run
+// did not build it
+static int64_t window_of(snn_ctx* c, uint32_t rank) {
+  const MapsState& m = ctx_maps(c);
+  if (rank < m.t0 || rank >= m.t0 + m.nt) {
+    ctx_fail(c, SNN_ESTATE, ("a dry run built only rank " + std::to_string(m.t0)).c_str());
+    return -1;
+  }
+  return (int64_t)(rank - m.t0);
+}
+
 int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp) {
   const Geom& g = ctx_geom(c);
   if (g.R == 1) {
@@ -645,7 +700,9 @@ int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp) {
     return SNN_OK;
   }
   MapsState& m = ctx_maps(c);
-  const uint64_t a = m.rows_off[rank], b = m.rows_off[rank + 1];
+  const int64_t w = window_of(c, rank);
+  if (w < 0) return SNN_ESTATE;
+  const uint64_t a = m.rows_off[w], b = m.rows_off[w + 1];
   rp->resize(b - a);
   MCK(cudaMemcpy(rp->data(), m.rows + a, (b - a) * 8, cudaMemcpyDeviceToHost));
   return SNN_OK;
@@ -660,10 +717,12 @@ int rank_row_scales(snn_ctx* c, uint32_t rank, std::vector<float>* scales) {
     return SNN_OK;
   }
   MapsState& m = ctx_maps(c);
+  const int64_t w = window_of(c, rank);
+  if (w < 0) return SNN_ESTATE;
   const uint32_t M = m.M[rank];
-  std::vector<uint32_t> gids(m.n_img[rank]);
+  std::vector<uint32_t> gids(m.n_img[w]);
   if (!gids.empty())
-    MCK(cudaMemcpy(gids.data(), m.img_gid + m.img_first[rank], gids.size() * 4, cudaMemcpyDeviceToHost));
+    MCK(cudaMemcpy(gids.data(), m.img_gid + m.img_first[w], gids.size() * 4, cudaMemcpyDeviceToHost));
   scales->assign(M + gids.size(), 1.0f);
   for (uint32_t s = 0; s < M; ++s) (*scales)[s] = src[(uint64_t)s * g.R + rank];
   for (size_t k = 0; k < gids.size(); ++k) (*scales)[M + k] = src[gids[k]];
@@ -681,14 +740,16 @@ int rank_row_bounds(snn_ctx* c, uint32_t rank, uint64_t row, uint64_t ab[2], flo
     return SNN_OK;
   }
   MapsState& m = ctx_maps(c);
-  const uint64_t nrows = m.rows_off[rank + 1] - m.rows_off[rank] - 1;
+  const int64_t w = window_of(c, rank);
+  if (w < 0) return SNN_ESTATE;
+  const uint64_t nrows = m.rows_off[w + 1] - m.rows_off[w] - 1;
   if (row >= nrows) return ctx_fail(c, SNN_EINVAL, "row out of range");
-  MCK(cudaMemcpy(ab, m.rows + m.rows_off[rank] + row, 16, cudaMemcpyDeviceToHost));
+  MCK(cudaMemcpy(ab, m.rows + m.rows_off[w] + row, 16, cudaMemcpyDeviceToHost));
   *scale = 1.0f;
   if (ctx_scale_src(c)) {
     uint32_t gid;
     if (row < m.M[rank]) gid = (uint32_t)(row * g.R + rank);
-    else MCK(cudaMemcpy(&gid, m.img_gid + m.img_first[rank] + (row - m.M[rank]), 4, cudaMemcpyDeviceToHost));
+    else MCK(cudaMemcpy(&gid, m.img_gid + m.img_first[w] + (row - m.M[rank]), 4, cudaMemcpyDeviceToHost));
     MCK(cudaMemcpy(scale, ctx_scale_src(c) + gid, 4, cudaMemcpyDeviceToHost));
   }
   return SNN_OK;
@@ -708,6 +769,8 @@ extern "C" int snn_get_maps(snn_ctx* c, uint32_t tau, uint32_t sigma, int32_t wh
   if (!m.rows) return ctx_fail(c, SNN_ESTATE, "no maps before calibrate");
   const uint32_t R = g.R;
   if (tau >= R || sigma >= R) return ctx_fail(c, SNN_EINVAL, "rank out of range");
+  if (m.dry && which != SNN_MAP_R && which != SNN_MAP_L)
+    return ctx_fail(c, SNN_ESTATE, "a dry run builds no source-side maps");
   std::vector<int64_t> out;
   auto fetch_u32 = [&](const uint32_t* p, uint64_t a, uint64_t b) -> int {
     std::vector<uint32_t> t(b - a);
@@ -720,10 +783,12 @@ extern "C" int snn_get_maps(snn_ctx* c, uint32_t tau, uint32_t sigma, int32_t wh
     case SNN_MAP_R:
     case SNN_MAP_L: {
       if (tau == sigma) break;
+      const int64_t w = window_of(c, tau);
+      if (w < 0) return SNN_ESTATE;
       const uint32_t slot = sigma < tau ? sigma + 1 : sigma;
-      const uint64_t a = m.img_off[(size_t)tau * (R + 1) + slot], b = m.img_off[(size_t)tau * (R + 1) + slot + 1];
+      const uint64_t a = m.img_off[(size_t)w * (R + 1) + slot], b = m.img_off[(size_t)w * (R + 1) + slot + 1];
       if (which == SNN_MAP_R) {
-        rc = fetch_u32(m.img_s, m.img_first[tau] + a, m.img_first[tau] + b);
+        rc = fetch_u32(m.img_s, m.img_first[w] + a, m.img_first[w] + b);
       } else {
         out.resize(b - a);
         for (uint64_t k = a; k < b; ++k) out[k - a] = (int64_t)m.M[tau] + (int64_t)k;

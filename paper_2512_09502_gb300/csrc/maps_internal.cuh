@@ -38,6 +38,8 @@ struct MapsState {
   uint64_t* h_pos = nullptr; std::vector<uint64_t> h_off; uint64_t* d_h_off = nullptr;
   uint32_t* H = nullptr; int32_t* I = nullptr; uint64_t n_h = 0;
   RouteArgs route{};
+  uint32_t t0 = 0, nt = 0;              // ranks the target-side arrays cover: t0 .. t0 + nt - 1
+  bool dry = false;                     // one rank's share only: no source-side maps
 };
 
 // accessors of the context (api.cu)
@@ -61,6 +63,7 @@ uint32_t* ctx_err(snn_ctx* c);
 int ctx_exchange(snn_ctx* c);
 uint32_t ctx_N(snn_ctx* c);
 
+int build_maps_dry(snn_ctx* c, uint32_t rank);   // target side of one rank (dry run)
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs,
                const uint64_t* d_cbase);
 int setup_routing(snn_ctx* c);

@@ -219,6 +219,7 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   a.dense_off = sc->dense_off;
   a.tgt = dev_tgt; a.w = dev_w; a.d = dev_d; a.w_format = 0;
   a.dense = dev_row_ptr; a.row_scale_src = nullptr;
+  a.dense_seg0 = 0; a.dense_nseg = 1;
   a.fuse_hist = 1;
   a.sort_items = 0;                        // records per thread giving kTile-record tiles
   for (uint32_t it : {8u, 12u, 16u})

@@ -157,7 +157,8 @@ struct BuildArgs {
   uint64_t n_sort_tiles;
   const uint64_t* cbase_sorted;   // [nproj] cbase of projections in id order
   uint32_t* tgt; void* w; uint8_t* d; uint32_t w_format;
-  uint64_t* dense;          // [R][N+1] row starts (absolute)
+  uint64_t* dense;          // [dense_nseg][N+1] row starts (absolute) of segments dense_seg0 ..
+  uint32_t dense_seg0, dense_nseg;   // all ranks: 0, R; a dry run: its one rank
   const uint32_t* dense_off;  // [R][R]
   const float* row_scale_src; // per source gid (fp16 format) or null
   int num_sms;
