@@ -414,12 +414,14 @@ int snn_calibrate(snn_ctx* c) {
   c->rank_off.assign(R + 1, 0);
   for (uint32_t t = 0; t < R; ++t) c->M[t] = (N - t + R - 1) / R;
   for (uint32_t t = 0; t < R; ++t) c->rank_off[t + 1] = c->rank_off[t] + c->M[t];
-  c->host_gid_of.resize(N);
-  c->host_pos_of.resize(N);
-  for (uint32_t gid = 0; gid < N; ++gid) {
-    const uint32_t pos = c->rank_off[gid % R] + gid / R;
-    c->host_gid_of[pos] = gid;
-    c->host_pos_of[gid] = pos;
+  if (!c->cfg.dry_run) {           // per-neuron maps serve the simulation state only
+    c->host_gid_of.resize(N);
+    c->host_pos_of.resize(N);
+    for (uint32_t gid = 0; gid < N; ++gid) {
+      const uint32_t pos = c->rank_off[gid % R] + gid / R;
+      c->host_gid_of[pos] = gid;
+      c->host_pos_of[gid] = pos;
+    }
   }
 
   // ---- projections, counters, delay tables ----
@@ -460,7 +462,8 @@ int snn_calibrate(snn_ctx* c) {
   g.key_bits = g.rb + g.sb + g.db;
   g.cbits = std::max(1u, bits_for(ctot ? ctot - 1 : 0));
   g.magic_R = magic_for(R);
-  if (g.key_bits + g.cbits > 64) return fail(c, SNN_EINVAL, "network too large for 64-bit sort records");
+  if (g.key_bits + g.cbits > 64 && !c->cfg.dry_run)
+    return fail(c, SNN_EINVAL, "network too large for 64-bit sort records");
   // pass plan: as few passes as digits of at most radix_bits allow, 8-bit digits
   // wherever possible (a 9-bit pass costs more than an 8-bit one)
   const uint32_t RB = (uint32_t)c->cfg.radix_bits;
@@ -583,6 +586,11 @@ int snn_calibrate(snn_ctx* c) {
   c->seg_start[R] = pos;
   const uint64_t E = pos;
   c->E = E;
+  if (dry) {
+    // records carry their generation position within the one built rank
+    g.cbits = std::max(1u, bits_for(E ? E - 1 : 0));
+    if (g.key_bits + g.cbits > 64) return fail(c, SNN_EINVAL, "rank share too large for 64-bit sort records");
+  }
   const uint64_t SORT_TILE = sort_tile_items((uint32_t)c->cfg.sort_items);
   std::vector<uint64_t> seg_tile0(R + 1, 0);
   for (uint32_t t = 0; t < R; ++t)
@@ -638,6 +646,7 @@ int snn_calibrate(snn_ctx* c) {
   a.n_sort_tiles = n_sort_tiles; a.cbase_sorted = d_cbase; a.num_sms = c->num_sms;
   a.dense_off = c->d_dense_off;
   a.fuse_hist = counted ? 0u : 1u;
+  a.pos_counters = dry ? 1u : 0u;
   a.sort_items = (uint32_t)c->cfg.sort_items;
   for (int p = 0; p < 8; ++p) { a.pass_bits[p] = pass_bits[p]; a.pass_shift[p] = pass_shift[p]; }
 

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       uint32_t d = P.d_const;
       if (P.d_kind == 1) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
       const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
-      a.rec_a[blk.out_base + e] = (kk << g.cbits) | ((P.cbase + c) & cmask);
+      const uint64_t cid = a.pos_counters ? blk.out_base + e : P.cbase + c;
+      a.rec_a[blk.out_base + e] = (kk << g.cbits) | (cid & cmask);
       if (hist) {
         const uint32_t k32 = (uint32_t)kk;
 #pragma unroll
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
       const uint32_t ps = (uint32_t)(kp >> (g.db + g.sb));
       prow = ps < g.R ? (int64_t)((uint64_t)doff[ps] + ((kp >> g.db) & smask)) : (int64_t)g.N;
     }
-    uint32_t p = 0;
+    uint32_t p = 0, blk_i = 0;
     uint64_t p_lo = 0, p_hi = 0;   // counters [p_lo, p_hi) of the cached projection p (none yet)
     uint32_t tl[FIN_Q], wb[FIN_Q], dd[FIN_Q];
     bool ok[FIN_Q];
@@ -799,22 +800,52 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
       prow = (int64_t)row;
 
       // projection of the counter, then target and weight regenerated from it
-      if (cidx - p_lo >= p_hi - p_lo) {
-        p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
-        p_lo = a.cbase_sorted[p];
-        p_hi = p + 1 < a.nproj ? a.cbase_sorted[p + 1] : ~0ull;
+      uint64_t c;
+      uint32_t t;
+      if (a.pos_counters) {
+        // generation position: its block gives projection, first target and target step
+        if (cidx - p_lo >= p_hi - p_lo) {
+          uint32_t lo = 0, hi = a.nblocks;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.blocks[mid].out_base <= cidx) lo = mid + 1; else hi = mid;
+          }
+          blk_i = lo - 1;
+          p_lo = a.blocks[blk_i].out_base;
+          p_hi = p_lo + a.blocks[blk_i].count;
+          p = a.blocks[blk_i].proj;
+        }
+        const DevBlock& B = a.blocks[blk_i];
+        const DevProj& Q = a.projs[p];
+        const uint64_t l = cidx - B.out_base;
+        if (Q.rule == kRuleFixedIndegree) {
+          const uint64_t m = div_magic(l, Q.K, Q.magic_div);
+          const uint64_t ti = B.ti0 + m * B.tstep;
+          c = ti * Q.K + (l - m * Q.K);
+          t = Q.tgt_first + (uint32_t)ti * Q.tgt_stride;
+        } else {                       // fixed total on one rank: the draw index
+          c = l;
+          const uint4 bt = philox_stream(c, Q.proj_id, kPurposeFtTarget, Q.seed);
+          t = Q.tgt_first + uniform_index(bt.x, Q.n_tgt) * Q.tgt_stride;
+        }
+      } else {
+        if (cidx - p_lo >= p_hi - p_lo) {
+          p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
+          p_lo = a.cbase_sorted[p];
+          p_hi = p + 1 < a.nproj ? a.cbase_sorted[p + 1] : ~0ull;
+        }
+        const DevProj& Q = a.projs[p];
+        c = cidx - Q.cbase;
+        if (Q.rule == kRuleFixedIndegree) {
+          t = Q.tgt_first + (uint32_t)div_magic(c, Q.K, Q.magic_div) * Q.tgt_stride;
+        } else if (Q.rule == kRuleFixedTotal) {
+          const uint4 bt = philox_stream(c, Q.proj_id, kPurposeFtTarget, Q.seed);
+          t = Q.tgt_first + uniform_index(bt.x, Q.n_tgt) * Q.tgt_stride;
+        } else {
+          t = Q.tgt_first + (uint32_t)div_magic(c, Q.n_src, Q.magic_div) * Q.tgt_stride;
+        }
       }
       const DevProj& P = a.projs[p];
-      const uint64_t c = cidx - P.cbase;
-      uint32_t t;
-      if (P.rule == kRuleFixedIndegree) {
-        t = P.tgt_first + (uint32_t)div_magic(c, P.K, P.magic_div) * P.tgt_stride;
-      } else if (P.rule == kRuleFixedTotal) {
-        const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);
-        t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
-      } else {
-        t = P.tgt_first + (uint32_t)div_magic(c, P.n_src, P.magic_div) * P.tgt_stride;
-      }
       tl[j] = g.R == 1 ? t : (uint32_t)div_magic(t, g.R, g.magic_R);
       dd[j] = d;
       const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);

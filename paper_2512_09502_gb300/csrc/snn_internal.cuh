@@ -163,6 +163,8 @@ struct BuildArgs {
   const float* row_scale_src; // per source gid (fp16 format) or null
   int num_sms;
   uint32_t fuse_hist;         // generation accumulates the sort histograms itself
+  uint32_t pos_counters;      // records carry their generation position, not the counter
+                              // (one uncounted block per projection: a dry run)
   uint32_t sort_items;        // records per thread of a sort tile (tile = 256 x items)
   // pass plan: digit p is (key >> pass_shift[p]) & ((1 << pass_bits[p]) - 1); histogram
   // and bin arrays use kHistStride bins per pass
