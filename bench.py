@@ -40,7 +40,8 @@ BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize
                                                   # merged ring (tau_ex == tau_in): no I_in traffic
 
 
-WORKLOADS = ("balanced_500k", "balanced_5k", "multi_area", "multi_area_r128")
+WORKLOADS = ("balanced_500k", "balanced_5k", "multi_area", "multi_area_r128", "indegree_x2", "indegree_x5",
+             "indegree_x10")
 
 
 def workload(name: str, scale: float):
@@ -53,6 +54,8 @@ def workload(name: str, scale: float):
         return wl.multi_area(scale=scale)
     if name == "multi_area_r128":       # the same network over 128 logical ranks
         return wl.multi_area(scale=scale, n_ranks=128)
+    if name.startswith("indegree_x"):    # 5.625G synapses with K = 11,250 x factor
+        return wl.indegree_scaling(int(name[len("indegree_x"):]), neurons_at_1=int(500_000 * scale))
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -162,6 +162,18 @@ DRIVE_SMALL_HZ = 10200.0
 DRIVE_SCALED_HZ = 20000.0
 
 
+def indegree_scaling(factor: int, neurons_at_1: int = 500_000, **kw) -> Network:
+    """The balanced network with in-degree scaled up by ``factor`` and the neuron count
+    and recurrent weights scaled down by it, so that synapses and the input per neuron
+    (K x J) stay fixed (paper, Appendix "Scalable balanced network with different
+    in-degree scale parameter"): K = (9,000 + 2,250) x factor; at factor 1 it is the
+    500k-neuron workload."""
+    kw.setdefault("drive_rate_hz", DRIVE_SCALED_HZ)
+    n = neurons_at_1 // factor
+    return balanced(n * 4 // 5, n - n * 4 // 5, 9000 * factor, 2250 * factor, DELAY_NORMAL,
+                    name=f"indegree_x{factor}", j_scale=1.0 / factor, **kw)
+
+
 def balanced_small(**kw) -> Network:
     """5,000 neurons, K = 400 E + 100 I, constant 1.5 ms delay, 2.5M synapses."""
     kw.setdefault("drive_rate_hz", DRIVE_SMALL_HZ)

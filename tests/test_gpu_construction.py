@@ -34,6 +34,14 @@ def test_ragged_sizes_normal_delays(ne, ni, ke, ki):
     _check(wl.balanced(ne, ni, ke, ki, wl.DELAY_NORMAL, seed=ne))
 
 
+def test_indegree_beyond_source_count():
+    """In-degree scaling (the paper's appendix on in-degree): K = 10x the neurons' count
+    of its population, so every target draws each source ~10 times (multapses)."""
+    net = wl.indegree_scaling(10, neurons_at_1=1000)
+    assert net.projections[0].rule.param == 90000 and net.populations[0].n == 80
+    _check(net)
+
+
 def test_delay_tables_match_oracle():
     from oracle import sampling as sm
     net = wl.balanced(300, 75, 40, 10, wl.DELAY_NORMAL)
