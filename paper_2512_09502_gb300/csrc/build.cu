@@ -42,9 +42,11 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // indexed search) holds the count at the start of each 2^24-wide window of w, so the
 // search starts there and needs at most a few compares; the result equals a plain
 // binary search.
+constexpr int GUIDE_BITS = 12;      // guide cells: the top 12 bits of the uniform word
+
 __device__ __forceinline__ uint32_t guided_count(const uint32_t* thr, uint32_t len, const uint8_t* guide,
                                                  uint32_t w) {
-  uint32_t c = guide[w >> 24];
+  uint32_t c = guide[w >> (32 - GUIDE_BITS)];
   while (c < len && thr[c] <= w) ++c;
   return c;
 }
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
   __shared__ uint32_t s_tbl[256];
-  __shared__ uint8_t s_guide[256];
+  __shared__ uint8_t s_guide[1 << GUIDE_BITS];
   __shared__ DevBlock s_blk;
   __shared__ DevProj s_proj;
   const int tid = threadIdx.x;
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   int cur_rank = -1;
   const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
 
+  uint32_t cur_tbl = 0xFFFFFFFFu;      // delay table staged in s_tbl / s_guide
   for (uint64_t tile = t0; tile < t1; ++tile) {
     __syncthreads();
     if (tid == 0) {
@@ -99,12 +102,15 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       }
       cur_rank = blk.rank;
     }
-    if (P.d_kind == 1)
+    if (P.d_kind == 1 && P.d_tbl_off != cur_tbl) {   // block-uniform: P is shared
+      // stage the delay table and its guide only when the projection's table changes
       for (uint32_t i = tid; i < P.d_tbl_len; i += GEN_BLOCK) s_tbl[i] = a.dtables[P.d_tbl_off + i];
-    __syncthreads();
-    if (P.d_kind == 1)
-      s_guide[tid] = (uint8_t)upper_bound_u32(s_tbl, P.d_tbl_len, (uint32_t)tid << 24);   // 256 threads
-    __syncthreads();
+      __syncthreads();
+      for (uint32_t cell = tid; cell < (1u << GUIDE_BITS); cell += GEN_BLOCK)
+        s_guide[cell] = (uint8_t)upper_bound_u32(s_tbl, P.d_tbl_len, cell << (32 - GUIDE_BITS));
+      __syncthreads();
+      cur_tbl = P.d_tbl_off;
+    }
 
     const uint64_t e0 = (tile - blk.tile_first) * (uint64_t)GEN_TILE;
     const uint32_t n = (uint32_t)min((uint64_t)GEN_TILE, blk.count - e0);
