@@ -12,9 +12,10 @@
 //                    order into their rank segment, with the digit histograms of every
 //                    sort pass accumulated on the fly (no extra read of the records);
 //   bin_scan_kernel  exclusive scan of the histograms -> global bin bases;
-//   onesweep_pass    one stable LSD pass per digit: warp-level multisplit ranking,
-//                    decoupled look-back over tiles (bounded spin), shared-memory
-//                    staging so that each digit run is written contiguously;
+//   onesweep_pass    one stable LSD pass per digit over 8,192-record tiles: warp
+//                    ranking from digit-bit ballots, shared-memory staging so that each
+//                    digit run is written contiguously, then a decoupled look-back over
+//                    the segment's earlier tiles (bounded spin) for the global offsets;
 //   finalize_kernel  decodes the sorted records: rank-local target, weight
 //                    (regenerated from the counter), delay; writes the SoA arrays and
 //                    the dense row starts (the CSR) from record boundaries.

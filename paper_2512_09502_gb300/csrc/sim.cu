@@ -14,7 +14,9 @@
 //
 // One step = update_kernel (reads and clears ring slot n, integrates, appends spikes
 // to the per-step delivery list) then deliver_kernel (walks the rows of every listed
-// spike and red.add's the weights into slots n + d).  The step needs no host involvement
+// spike and red.add's the weights into slots n + d; a CTA per row slice for the long
+// rows of one rank, deliver_rows_kernel's lane groups for the short image rows of many
+// ranks).  The step needs no host involvement
 // and is captured as a CUDA graph.  The step index of a launch is *step + k, with k baked
 // into the launch (or graph node); one advance kernel after a batch of steps adds the
 // batch length, so no per-step completion handshake is needed.
