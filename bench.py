@@ -119,11 +119,11 @@ class Clocks:
 # source file and its sha256[:16] at capture time; profiles/traffic_balanced_500k.md
 # gives the commands and the raw figures.
 TRAFFIC = {
-    "deliver_kernel": {"bytes_per_unit": 22.53, "source": "sim.cu", "source_sha": "c955d0eb71afd827"},
-    "update_kernel": {"bytes_per_unit": 16.06, "source": "sim.cu", "source_sha": "c955d0eb71afd827"},
-    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "2fa3f514017b4b35"},
-    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "source_sha": "2fa3f514017b4b35"},
-    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "source_sha": "2fa3f514017b4b35"},
+    "deliver_kernel": {"bytes_per_unit": 22.53, "source": "sim.cu", "source_sha": "853ed517c4f56b4b"},
+    "update_kernel": {"bytes_per_unit": 16.06, "source": "sim.cu", "source_sha": "853ed517c4f56b4b"},
+    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "ba19e85393e03736"},
+    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "source_sha": "ba19e85393e03736"},
+    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "source_sha": "ba19e85393e03736"},
 }
 
 
