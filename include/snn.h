@@ -52,6 +52,9 @@ extern "C" {
 #define SNN_RULE_FIXED_INDEGREE 0     /* param = K: K sources per target            */
 #define SNN_RULE_FIXED_TOTAL 1        /* param = N: N (source, target) draws        */
 #define SNN_RULE_PAIRWISE_BERNOULLI 2 /* param = p: each pair kept with prob. p    */
+/* param = p: each pair kept with probability p, drawn as geometric gaps between kept
+   sources (one draw per kept pair instead of one test per pair; p >= ~5e-6) */
+#define SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC 3
 
 #define SNN_W_CONST 0        /* weight = mean                                          */
 #define SNN_W_NORMAL_SIGN 1  /* normal(mean, sd), clamped at 0 to keep mean's sign    */

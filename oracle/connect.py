@@ -14,14 +14,15 @@ Readings (the paper does not fix the generator):
   is the projection-local counter:
     - fixed in-degree K:   c = (t - t_first) * K + k, for target t, k < K;
     - fixed total N:       c = j, the draw index;
-    - pairwise Bernoulli:  c = q = i_t * n_src + i_s.
+    - pairwise Bernoulli:  c = q = i_t * n_src + i_s (both variants).
   Sources and targets are the projection's i-th members src_first + i * src_stride
   and tgt_first + i * tgt_stride (stride 1 for population ranges; a rank-local range
   of a round-robin partition has stride R).
 * Words of the SYNAPSE block: w0 -> source index, w1 -> delay step, (w2, w3) ->
   weight.  A fixed-total draw takes its target from w0 of the FT_TARGET block.  A
   Bernoulli pair q is kept iff word (q & 3) of the PB_TEST block at counter q >> 2 is
-  below floor(p 2^32) (all pairs when p = 1).
+  below floor(p 2^32) (all pairs when p = 1).  The geometric-skipping variant draws
+  the gaps between kept pairs instead (``bernoulli_geometric_pairs``).
 * Generation order is (projection order, c ascending).  ``gidx`` = cbase_p + c, with
   cbase_p the summed counter-space sizes (n_tgt K, N, n_tgt n_src) of earlier
   projections; it is the tie-break of the source-sorted layout.
@@ -49,7 +50,7 @@ def counter_space(pr) -> int:
         return int(pr.rule.param) * pr.n_tgt
     if pr.rule.kind == "fixed_total":
         return int(pr.rule.param)
-    if pr.rule.kind == "pairwise_bernoulli":
+    if pr.rule.kind in ("pairwise_bernoulli", "pairwise_bernoulli_geometric"):
         return pr.n_tgt * pr.n_src
     raise ValueError(pr.rule.kind)
 
@@ -88,6 +89,12 @@ def projection_synapses(net, pid: int, counters=None):
         bt = ph.stream(c, pid, ph.PURPOSE_FT_TARGET, pr.seed)
         src = pr.src_first + pr.src_stride * sm.uniform_index(b[0], pr.n_src).astype(np.int64)
         tgt = pr.tgt_first + pr.tgt_stride * sm.uniform_index(bt[0], pr.n_tgt).astype(np.int64)
+    elif kind == "pairwise_bernoulli_geometric":
+        assert counters is None
+        c = bernoulli_geometric_pairs(pr, pid)
+        b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
+        src = pr.src_first + pr.src_stride * (c % np.uint64(pr.n_src)).astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * (c // np.uint64(pr.n_src)).astype(np.int64)
     elif kind == "pairwise_bernoulli":
         assert counters is None
         q = np.arange(pr.n_tgt * pr.n_src, dtype=np.uint64)
@@ -104,6 +111,28 @@ def projection_synapses(net, pid: int, counters=None):
     d = sm.delay_steps(pr.delay, net.dt, b[1], len(c))
     w = sm.weight_values(pr.weight, b[2], b[3], len(c))
     return dict(src=src, tgt=tgt, d=d, w=w, c=c.astype(np.int64))
+
+
+def bernoulli_geometric_pairs(pr, pid: int):
+    """Kept pairs q = i_t * n_src + i_s of pairwise Bernoulli by geometric skipping, in
+    (target, source) order.  For target i_t the j-th gap G_j inverts word w0 of the
+    PB_GAP block at counter i_t * n_src + j through the gap table; the kept sources are
+    s_j = sum_{i <= j} (G_i + 1) - 1 while below n_src.  Each pair is kept with
+    probability p, independently, as in the pair-by-pair rule, at a cost of one draw
+    per kept pair (plus one) instead of one per pair."""
+    p = float(pr.rule.param)
+    if p == 0.0:
+        return np.zeros(0, dtype=np.uint64)
+    thr = sm.geometric_gap_table(p)
+    out = []
+    n = pr.n_src
+    for ti in range(pr.n_tgt):
+        ctr = np.uint64(ti * n) + np.arange(n, dtype=np.uint64)
+        g = sm.inverse_table(thr, ph.stream(ctr, pid, ph.PURPOSE_PB_GAP, pr.seed)[0])
+        s = np.cumsum(g + 1) - 1
+        s = s[s < n]
+        out.append(np.uint64(ti * n) + s.astype(np.uint64))
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.uint64)
 
 
 def generate(net):

@@ -33,6 +33,7 @@ PURPOSE_FT_TARGET = 1    # target choice of a fixed-total draw
 PURPOSE_PB_TEST = 2      # inclusion test of pairwise Bernoulli (4 pairs per call)
 PURPOSE_POISSON = 3      # Poisson drive counts of four consecutive neurons in one step
 PURPOSE_VINIT = 4        # initial membrane potential
+PURPOSE_PB_GAP = 5       # gap between kept pairs of pairwise Bernoulli by geometric skipping
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

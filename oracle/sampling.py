@@ -125,6 +125,31 @@ def poisson_table(rate_hz: float, dt: float):
     return np.array(thr, dtype=np.uint64)
 
 
+MAX_GAP_TABLE = 1 << 22
+
+
+def geometric_gap_table(p: float):
+    """Integer CDF table of the gap G >= 0 between kept pairs when every pair is kept
+    with probability p: P(G <= g) = 1 - (1 - p)^(g + 1), so G(w) = #{i : w >= thr[i]}.
+    The power is accumulated by repeated multiplication in fp64, which rounds the same
+    way in every IEEE implementation.  The table stops at the first threshold that
+    reaches 2^32; p must be in (0, 1] and the table at most 2^22 entries long."""
+    if not 0.0 < p <= 1.0:
+        raise ValueError("p must be in (0, 1]")
+    q = 1.0 - p
+    qq = q
+    thr = []
+    while True:
+        c = _cdf_threshold(1.0 - qq)
+        if c >= 4294967296:
+            break
+        thr.append(c)
+        if len(thr) > MAX_GAP_TABLE:
+            raise ValueError("connection probability too small for the gap table")
+        qq = qq * q
+    return np.array(thr, dtype=np.uint64)
+
+
 def inverse_table(thr, w):
     """#{i : w >= thr[i]} for a non-decreasing threshold table."""
     return np.searchsorted(np.asarray(thr, dtype=np.uint64), np.asarray(w, dtype=np.uint64),

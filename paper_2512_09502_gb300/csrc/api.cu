@@ -40,6 +40,7 @@ struct ProjSpec {
   // derived at calibrate
   uint32_t d_smin = 0;
   std::vector<uint32_t> d_thr;
+  std::vector<uint32_t> g_thr;   // gap table (pairwise Bernoulli by geometric gaps)
 };
 struct DriveSpec {
   uint32_t first, n;
@@ -258,6 +259,24 @@ DevPop propagators(const snn_iaf_psc_exp_params& p, double h) {
   return o;
 }
 
+// Integer CDF table of the gap G >= 0 between kept pairs (pairwise Bernoulli by
+// geometric gaps): thr_g = floor(P(G <= g) 2^32 + 1/2), P(G <= g) = 1 - (1 - p)^(g + 1)
+// with the power accumulated by repeated fp64 multiplication; the table stops at the
+// first threshold reaching 2^32 and holds at most 2^22 entries.
+int gap_table(double p, std::vector<uint32_t>* thr) {
+  thr->clear();
+  const double q = 1.0 - p;
+  double qq = q;
+  while (true) {
+    const double v = std::floor((1.0 - qq) * 4294967296.0 + 0.5);
+    if (v >= 4294967296.0) break;
+    thr->push_back((uint32_t)v);
+    if (thr->size() > (size_t)1 << 22) return SNN_EINVAL;
+    qq = qq * q;
+  }
+  return SNN_OK;
+}
+
 uint64_t counter_space(const ProjSpec& p) {
   switch (p.rule.kind) {
     case SNN_RULE_FIXED_INDEGREE: return (uint64_t)p.rule.param * p.n_tgt;
@@ -350,6 +369,11 @@ static int add_projection(snn_ctx* c, uint32_t src_first, uint32_t n_src, uint32
     case SNN_RULE_PAIRWISE_BERNOULLI:
       if (!(rule->param >= 0 && rule->param <= 1)) return fail(c, SNN_EINVAL, "Bernoulli p outside [0, 1]");
       break;
+    case SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC:
+      if (!(rule->param >= 0 && rule->param <= 1)) return fail(c, SNN_EINVAL, "Bernoulli p outside [0, 1]");
+      if (rule->param > 0 && gap_table(rule->param, &p.g_thr) != SNN_OK)
+        return fail(c, SNN_EINVAL, "connection probability too small for the gap table");
+      break;
     default:
       return fail(c, SNN_EINVAL, "unknown rule");
   }
@@ -439,7 +463,8 @@ int snn_calibrate(snn_ctx* c) {
     d.rule = (uint32_t)s.rule.kind; d.proj_id = i; d.seed = s.seed;
     d.K = s.rule.kind == SNN_RULE_FIXED_INDEGREE ? (uint64_t)s.rule.param : 0;
     d.N = s.rule.kind == SNN_RULE_FIXED_TOTAL ? (uint64_t)s.rule.param : 0;
-    d.pb_thr = s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI ? (uint64_t)std::floor(s.rule.param * 4294967296.0) : 0;
+    d.pb_thr = (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI || s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC)
+                   ? (uint64_t)std::floor(s.rule.param * 4294967296.0) : 0;
     d.cbase = ctot; d.csize = counter_space(s);
     c->cbase[i] = ctot;
     ctot += d.csize;
@@ -450,6 +475,8 @@ int snn_calibrate(snn_ctx* c) {
     d.d_const = s.d_smin;
     d.d_tbl_off = (uint32_t)dtab.size(); d.d_tbl_len = (uint32_t)s.d_thr.size();
     dtab.insert(dtab.end(), s.d_thr.begin(), s.d_thr.end());
+    d.g_tbl_off = (uint32_t)dtab.size(); d.g_tbl_len = (uint32_t)s.g_thr.size();
+    dtab.insert(dtab.end(), s.g_thr.begin(), s.g_thr.end());
     dmax = std::max(dmax, s.d_smin + (uint32_t)s.d_thr.size());
   }
   uint32_t maxM = 0;
@@ -487,6 +514,8 @@ int snn_calibrate(snn_ctx* c) {
   // ---- counted projections: fixed total over several ranks, pairwise Bernoulli ----
   DevProj* d_projs;
   UP(d_projs, dp, "projections");
+  uint32_t* d_dtab;
+  UP(d_dtab, dtab, "delay and gap tables");
   std::vector<uint32_t> ft_proj, pb_proj;
   std::vector<uint64_t> ft_tile_first(1, 0), pb_t_first(1, 0);
   for (uint32_t i = 0; i < P; ++i) {
@@ -494,7 +523,7 @@ int snn_calibrate(snn_ctx* c) {
     if (s.rule.kind == SNN_RULE_FIXED_TOTAL && R > 1) {
       ft_proj.push_back(i);
       ft_tile_first.push_back(ft_tile_first.back() + ((uint64_t)s.rule.param + kCountTile - 1) / kCountTile);
-    } else if (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI) {
+    } else if (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI || s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC) {
       pb_proj.push_back(i);
       pb_t_first.push_back(pb_t_first.back() + s.n_tgt);
     }
@@ -516,7 +545,7 @@ int snn_calibrate(snn_ctx* c) {
     UP(d_pbp, pb_proj, "Bernoulli list");
     UP(d_ftf, ft_tile_first, "fixed-total tiles");
     UP(d_pbf, pb_t_first, "Bernoulli targets");
-    ca.projs = d_projs; ca.R = R; ca.magic_R = magic_for(R);
+    ca.projs = d_projs; ca.R = R; ca.magic_R = magic_for(R); ca.tables = d_dtab;
     ca.ft_proj = d_ftp; ca.ft_tile_first = d_ftf; ca.n_ft = (uint32_t)ft_proj.size();
     ca.n_ft_tiles = ft_tile_first.back();
     ca.pb_proj = d_pbp; ca.pb_t_first = d_pbf; ca.n_pb = (uint32_t)pb_proj.size();
@@ -554,7 +583,8 @@ int snn_calibrate(snn_ctx* c) {
     for (uint32_t i = 0; i < P; ++i) {
       const ProjSpec& s = c->projs[i];
       const bool is_ft_counted = s.rule.kind == SNN_RULE_FIXED_TOTAL && R > 1;
-      const bool is_pb = s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI;
+      const bool is_pb = s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI ||
+                         s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC;
       if (counted) block_base[(size_t)i * R + t] = pos;
       if (is_ft_counted || is_pb) {
         const uint32_t q = is_pb ? kpb++ : kft++;
@@ -610,7 +640,7 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- device buffers for the build ----
   BuildArgs a{};
-  DevBlock* d_blocks; uint32_t* d_dtab; uint64_t* d_seg_tile0; uint64_t* d_cbase;
+  DevBlock* d_blocks; uint64_t* d_seg_tile0; uint64_t* d_cbase;
   UP(d_blocks, blocks, "blocks");
   if (counted) {
     uint64_t* d_bb;
@@ -618,7 +648,6 @@ int snn_calibrate(snn_ctx* c) {
     ca.block_base = d_bb;
     counted_bufs.push_back(d_bb);
   }
-  UP(d_dtab, dtab, "delay tables");
   UP(c->d_seg_start, c->seg_start, "segments");
   UP(d_seg_tile0, seg_tile0, "sort tiles");
   UP(d_cbase, c->cbase, "counter bases");
@@ -712,7 +741,7 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- image neurons and communication maps (logical ranks) ----
   if (R > 1) {
-    int rc = dry ? build_maps_dry(c, dr) : build_maps(c, dp, d_projs, d_cbase);
+    int rc = dry ? build_maps_dry(c, dr) : build_maps(c, dp, d_projs, d_cbase, d_dtab);
     if (rc != SNN_OK) return rc;
   }
   CK(cudaEventRecord(ev[4], c->st));

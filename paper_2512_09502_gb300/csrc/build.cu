@@ -518,6 +518,34 @@ __global__ void ft_scan_kernel(CountedArgs c) {
 }
 
 // one warp per target of a Bernoulli projection: pairs kept
+// Pairwise Bernoulli by geometric gaps, one warp per target ti: lane l of a round draws
+// gap j = j0 + l (word x of the PB_GAP block at counter ti * n_src + j, inverted through
+// the gap table) and the warp's prefix sum of (gap + 1) gives the kept sources s_j in
+// ascending order; the walk ends with the first round that passes n_src.  Every lane
+// calls round(s, kept, mask, rank): kept lanes form a prefix of the warp, mask is the
+// ballot of kept lanes and rank the lane's position among them.
+template <typename Fn>
+__device__ __forceinline__ void geometric_walk(const DevProj& P, const uint32_t* tbl, uint64_t ti, Fn round) {
+  const uint32_t lane = threadIdx.x & 31;
+  int64_t base = -1;                          // last kept source before this round
+  for (uint64_t j0 = 0;; j0 += 32) {
+    const uint4 b = philox_stream(ti * P.n_src + j0 + lane, P.proj_id, kPurposePbGap, P.seed);
+    const uint64_t step = (uint64_t)upper_bound_u32(tbl, P.g_tbl_len, b.x) + 1;
+    uint64_t incl = step;                     // inclusive warp prefix sum of the steps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += v;
+    }
+    const int64_t s = base + (int64_t)incl;
+    const bool keep = s < (int64_t)P.n_src;
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    round(keep ? (uint32_t)s : 0u, keep, m, (uint32_t)__popc(m & ((1u << lane) - 1)));
+    if (m != 0xffffffffu) break;              // a source passed n_src: the walk is done
+    base += (int64_t)__shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
 __global__ void pb_count_kernel(CountedArgs c) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -527,10 +555,16 @@ __global__ void pb_count_kernel(CountedArgs c) {
     const DevProj& P = c.projs[c.pb_proj[q]];
     const uint64_t ti = x - c.pb_t_first[q];
     uint32_t cnt = 0;
-    for (uint32_t s0 = 0; s0 < P.n_src; s0 += 32) {
-      const uint32_t s = s0 + lane;
-      const bool keep = s < P.n_src && (uint64_t)pb_word(P, ti * P.n_src + s) < P.pb_thr;
-      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+    if (P.rule == kRuleBernoulliGeometric) {
+      if (P.pb_thr)
+        geometric_walk(P, c.tables + P.g_tbl_off, ti,
+                       [&](uint32_t, bool, uint32_t m, uint32_t) { cnt += __popc(m); });
+    } else {
+      for (uint32_t s0 = 0; s0 < P.n_src; s0 += 32) {
+        const uint32_t s = s0 + lane;
+        const bool keep = s < P.n_src && (uint64_t)pb_word(P, ti * P.n_src + s) < P.pb_thr;
+        cnt += __popc(__ballot_sync(0xffffffffu, keep));
+      }
     }
     if (lane == 0) c.pb_cnt[x] = cnt;
   }
@@ -639,6 +673,21 @@ __global__ void __launch_bounds__(256) pb_place_kernel(CountedArgs c, BuildArgs 
     const uint32_t rank = rank_of(t, c.R, c.magic_R);
     uint64_t pos = c.block_base[(uint64_t)pid * c.R + rank] + c.pb_off[x];
     const uint64_t end = a.seg_start[rank + 1];
+    if (P.rule == kRuleBernoulliGeometric) {
+      if (P.pb_thr)
+        geometric_walk(P, c.tables + P.g_tbl_off, ti, [&](uint32_t s, bool keep, uint32_t m, uint32_t r) {
+          if (keep) {
+            const uint64_t qq = ti * P.n_src + s;
+            const uint4 b = philox_stream(qq, P.proj_id, kPurposeSynapse, P.seed);
+            const uint32_t src = P.src_first + s * P.src_stride;
+            const uint64_t at = pos + r;
+            const uint64_t rr = make_record(P, a.g, rank, qq, src, b.y, a.dtables + P.d_tbl_off);
+            if (at < end) a.rec_a[at] = rr; else atomicOr(a.err, kErrBounds);
+          }
+          pos += __popc(m);
+        });
+      continue;
+    }
     for (uint32_t s0 = 0; s0 < P.n_src; s0 += 32) {
       const uint32_t s = s0 + lane;
       const uint64_t qq = ti * P.n_src + s;

@@ -159,7 +159,7 @@ __global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, uint32
 // ---- source side: regenerate every synapse's source and target rank ----
 __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_t* cbase,
                              uint64_t ctot, uint32_t R, uint64_t magic_R, uint32_t Mmax,
-                             uint8_t* flag /*[sigma][tau][Mmax]*/) {
+                             const uint32_t* tables, uint8_t* flag /*[sigma][tau][Mmax]*/) {
   __shared__ uint64_t s_cb[1024];
   const uint32_t ncache = nproj < 1024 ? nproj : 1024;
   for (uint32_t k = threadIdx.x; k < ncache; k += blockDim.x) s_cb[k] = cbase[k];
@@ -179,6 +179,24 @@ __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_
       const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);
       src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
       tgt = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
+    } else if (P.rule == kRuleBernoulliGeometric) {
+      // the thread of a target's first counter walks that target's gaps
+      if (!P.pb_thr) continue;
+      const uint64_t ti = div_magic(c, P.n_src, P.magic_div);
+      if (c != ti * P.n_src) continue;
+      tgt = P.tgt_first + (uint32_t)ti * P.tgt_stride;
+      const uint32_t tau = tgt - (uint32_t)div_magic(tgt, R, magic_R) * R;
+      const uint32_t* tbl = tables + P.g_tbl_off;
+      int64_t s_i = -1;
+      for (uint64_t j = 0;; ++j) {
+        const uint4 b = philox_stream(ti * P.n_src + j, P.proj_id, kPurposePbGap, P.seed);
+        s_i += (int64_t)upper_bound_u32(tbl, P.g_tbl_len, b.x) + 1;
+        if (s_i >= (int64_t)P.n_src) break;
+        src = P.src_first + (uint32_t)s_i * P.src_stride;
+        const uint32_t s = (uint32_t)div_magic(src, R, magic_R), sig = src - s * R;
+        if (sig != tau) flag[((uint64_t)sig * R + tau) * Mmax + s] = 1;
+      }
+      continue;
     } else {
       const uint4 tb = philox_stream(c >> 2, P.proj_id, kPurposePbTest, P.seed);
       const uint32_t lane = (uint32_t)(c & 3);
@@ -450,7 +468,8 @@ static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt) {
   return SNN_OK;
 }
 
-int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase) {
+int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase,
+               const uint32_t* d_tables) {
   MapsState& m = ctx_maps(c);
   cudaStream_t st = ctx_stream(c);
   const Geom& g = ctx_geom(c);
@@ -471,7 +490,7 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   for (const auto& p : projs) ctot = std::max(ctot, p.cbase + p.csize);
   if (ctot)
     source_flags<<<grid_for(c, ctot), MB, 0, st>>>(d_projs, (uint32_t)projs.size(), d_cbase, ctot, R, g.magic_R,
-                                                  Mmax, sflag);
+                                                  Mmax, d_tables, sflag);
   MCK(cudaGetLastError());
   uint32_t* f32v = alloc_n<uint32_t>(c, nf);
   m.spos = alloc_n<uint64_t>(c, nf + 1);

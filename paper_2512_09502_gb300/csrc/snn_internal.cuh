@@ -22,10 +22,12 @@ constexpr uint32_t kPurposeFtTarget = 1;
 constexpr uint32_t kPurposePbTest = 2;
 constexpr uint32_t kPurposePoisson = 3;
 constexpr uint32_t kPurposeVinit = 4;
+constexpr uint32_t kPurposePbGap = 5;
 
 constexpr uint32_t kRuleFixedIndegree = 0;
 constexpr uint32_t kRuleFixedTotal = 1;
 constexpr uint32_t kRulePairwiseBernoulli = 2;
+constexpr uint32_t kRuleBernoulliGeometric = 3;   // pairwise Bernoulli by geometric gaps
 
 // device error word bits
 constexpr uint32_t kErrTimeout = 1u;
@@ -89,6 +91,7 @@ struct DevProj {
   uint32_t d_kind;          // 0 const, 1 table
   uint32_t d_const;         // constant steps, or s_min of the table
   uint32_t d_tbl_off, d_tbl_len;
+  uint32_t g_tbl_off, g_tbl_len;   // gap table of pairwise Bernoulli by geometric gaps
 };
 
 // one generation block: the records of projection `proj` whose targets live on `rank`
@@ -193,6 +196,7 @@ struct CountedArgs {
   uint64_t* pb_off;               // [n_pb_targets] offset of the target within its block
   uint64_t* pb_tot;               // [n_pb][R]
   const uint64_t* block_base;     // [nproj][R] absolute first record of block (p, rank)
+  const uint32_t* tables;         // delay and gap tables (BuildArgs::dtables)
 };
 constexpr uint32_t kCountTile = 4096;
 constexpr uint32_t kMaxCountedRanks = 1024;

@@ -26,6 +26,7 @@ import numpy as np
 RULE_FIXED_INDEGREE = "fixed_indegree"
 RULE_FIXED_TOTAL = "fixed_total"
 RULE_PAIRWISE_BERNOULLI = "pairwise_bernoulli"
+RULE_PAIRWISE_BERNOULLI_GEOMETRIC = "pairwise_bernoulli_geometric"
 
 # weight distributions
 W_CONST = "const"

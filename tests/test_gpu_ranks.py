@@ -102,6 +102,23 @@ def test_pairwise_bernoulli(R):
         compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
 
 
+@pytest.mark.parametrize("R,p,n_src,n_tgt", [(1, 0.1, 300, 200), (3, 0.1, 300, 200), (2, 1.0, 45, 33),
+                                              (1, 0.0, 45, 33), (7, 0.013, 1000, 150), (1, 0.6, 77, 64)])
+def test_pairwise_bernoulli_geometric(R, p, n_src, n_tgt):
+    """Pairwise Bernoulli by geometric gaps: kept pairs, their order, delays and weights
+    bit-exact against the oracle's walk on one and several ranks (maps included)."""
+    net = wl.tiny(wl.RULE_PAIRWISE_BERNOULLI_GEOMETRIC, p, n_src=n_src, n_tgt=n_tgt, n_ranks=R)
+    ctx = gpu_build(net)
+    _, ref = oracle_layout(net)
+    for tau in range(R):
+        compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
+    for tau in range(R):
+        for sig in range(R):
+            if sig != tau:
+                np.testing.assert_array_equal(ctx.get_maps(tau, sig, "R"), ref["ranks"][tau]["R"][sig])
+                np.testing.assert_array_equal(ctx.get_maps(tau, sig, "S"), ref["S"][sig][tau])
+
+
 def test_fixed_total_over_ranks():
     net = wl.tiny(wl.RULE_FIXED_TOTAL, 50_000, n_src=300, n_tgt=200, n_ranks=4)
     ctx = gpu_build(net)

@@ -85,3 +85,66 @@ def test_partition_invariance_and_layout_order():
                 a, b = rp[r], rp[r + 1]
                 key = rk["d"][a:b] * (1 << 40) + rk["gidx"][a:b]
                 assert np.all(np.diff(key) > 0)
+
+
+def _geom_net(n_src, n_tgt, p, seed=5):
+    pr = wl.Projection(0, n_src, n_src, n_tgt, wl.Rule(wl.RULE_PAIRWISE_BERNOULLI_GEOMETRIC, p),
+                       wl.Dist(wl.W_CONST, 1.0, 0.0), wl.Dist(wl.D_CONST, 1.0), seed)
+    return wl.Network("geom", [wl.Population(n_src), wl.Population(n_tgt)], [pr], [])
+
+
+def test_geometric_gap_table_against_scipy():
+    """thr_g = round(P(G <= g) 2^32) for the number of failures before a success:
+    scipy's geom counts trials, so P(G <= g) = geom.cdf(g + 1)."""
+    from oracle import sampling as sm
+    for p in (0.5, 0.1, 0.013, 0.001):
+        thr = sm.geometric_gap_table(p)
+        g = np.arange(len(thr))
+        ref = np.floor(stats.geom.cdf(g + 1, p) * 2.0 ** 32 + 0.5)
+        assert np.abs(thr.astype(np.float64) - ref).max() <= 1.0
+        assert stats.geom.cdf(len(thr) + 1, p) * 2.0 ** 32 + 0.5 >= 2.0 ** 32 - 1   # stops at the top
+    assert len(sm.geometric_gap_table(1.0)) == 0           # p = 1: every gap is 0
+
+
+def test_geometric_bernoulli_limits_and_pair_independence():
+    """p = 1 keeps every pair; per-target counts follow Binomial(n_src, p); every source
+    is equally likely; gaps between kept sources are geometric; no multapses."""
+    all_pairs = oc.generate(_geom_net(13, 7, 1.0))
+    assert len(all_pairs["c"]) == 13 * 7
+    np.testing.assert_array_equal(all_pairs["c"], np.arange(13 * 7))
+    assert len(oc.generate(_geom_net(13, 7, 0.0))["c"]) == 0
+    n_src, n_tgt, p = 200, 400, 0.1
+    syn = oc.generate(_geom_net(n_src, n_tgt, p))
+    s = syn["src"]
+    t = syn["tgt"] - n_src
+    assert (np.diff(syn["c"]) > 0).all()                   # (target, source) order, no multapses
+    counts = np.bincount(t, minlength=n_tgt)
+    assert abs(counts.mean() - n_src * p) < 4 * np.sqrt(n_src * p * (1 - p) / n_tgt)
+    assert abs(counts.var() / (n_src * p * (1 - p)) - 1.0) < 0.25
+    src_hist = np.bincount(s, minlength=n_src)             # inclusion per source ~ Binomial(n_tgt, p)
+    chi2 = ((src_hist - n_tgt * p) ** 2 / (n_tgt * p)).sum()
+    assert stats.chi2.sf(chi2, n_src - 1) > 1e-3
+    gaps = []                                              # gaps between kept sources of a target
+    for k in range(n_tgt):
+        ss = np.sort(s[t == k])
+        gaps += list(np.diff(ss) - 1)
+    gaps = np.array(gaps)
+    kmax = 30
+    obs = np.array([np.count_nonzero(gaps == k) for k in range(kmax)] + [np.count_nonzero(gaps >= kmax)])
+    pmf = np.array([stats.geom.pmf(k + 1, p) for k in range(kmax)] + [stats.geom.sf(kmax, p)])
+    exp = pmf / pmf.sum() * len(gaps)
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    assert stats.chi2.sf(chi2, kmax) > 1e-3
+
+
+def test_geometric_and_pairwise_bernoulli_totals_agree():
+    """Both realizations of pairwise Bernoulli keep Binomial(n_src n_tgt, p) pairs."""
+    n_src, n_tgt, p = 300, 300, 0.05
+    tot_g = len(oc.generate(_geom_net(n_src, n_tgt, p, seed=9))["c"])
+    net_pb = _geom_net(n_src, n_tgt, p, seed=9)
+    net_pb.projections[0] = wl.Projection(0, n_src, n_src, n_tgt, wl.Rule(wl.RULE_PAIRWISE_BERNOULLI, p),
+                                          wl.Dist(wl.W_CONST, 1.0, 0.0), wl.Dist(wl.D_CONST, 1.0), 9)
+    tot_p = len(oc.generate(net_pb)["c"])
+    sd = np.sqrt(n_src * n_tgt * p * (1 - p))
+    for tot in (tot_g, tot_p):
+        assert abs(tot - n_src * n_tgt * p) < 4 * sd
