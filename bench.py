@@ -121,9 +121,9 @@ class Clocks:
 TRAFFIC = {
     "deliver_kernel": {"bytes_per_unit": 22.53, "source": "sim.cu", "source_sha": "853ed517c4f56b4b"},
     "update_kernel": {"bytes_per_unit": 16.06, "source": "sim.cu", "source_sha": "853ed517c4f56b4b"},
-    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "ba19e85393e03736"},
-    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "source_sha": "ba19e85393e03736"},
-    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "source_sha": "ba19e85393e03736"},
+    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
+    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
+    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
 }
 
 
