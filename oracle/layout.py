@@ -11,6 +11,9 @@ Definitions followed (paper, Methods, "Remote connections"):
   "Point-to-point MPI communication").  Only sources with at least one connection into
   tau get an image (the flagged variant of RemoteConnect, used for randomly drawn
   sources).
+* With the paper's threshold xi (Methods, "Remote connections") a projection whose
+  expected connections per source reach xi skips the flagging: all its sources get an
+  image on every rank holding its targets (``forced_images``); xi <= 0 keeps flagging.
 * Connections are sorted by source as the first key so that one source's outgoing
   connections are (first index, count) ("GPU memory levels"); the second key is the
   delay, and ties keep generation order (reading: stable sort, tie-break gidx).
@@ -59,11 +62,45 @@ def source_slot(sigma, tau):
     return np.where(sigma == tau, 0, np.where(sigma < tau, sigma + 1, sigma))
 
 
-def build_rank(syn, part, tau: int):
+def expected_per_source(pr) -> float:
+    """Expected connections per source of a projection, the quantity the paper's xi
+    heuristic compares (Methods, "Remote connections": K_in N_target / N_source for the
+    fixed in-degree rule)."""
+    if pr.rule.kind == "fixed_indegree":
+        return pr.rule.param * pr.n_tgt / pr.n_src
+    if pr.rule.kind == "fixed_total":
+        return pr.rule.param / pr.n_src
+    return pr.rule.param * pr.n_tgt                     # pairwise Bernoulli (both variants)
+
+
+def forced_images(net, part, xi: float):
+    """All-sources variant (xi > 0): a projection whose expected connections per source
+    reach xi gives every one of its sources an image on every rank holding one of its
+    targets, whether or not the source is used there.  Returns {tau: set of (sigma, s)}
+    with sigma != tau; empty sets for xi <= 0 (flagged images only)."""
+    R = part["R"]
+    out = {t: set() for t in range(R)}
+    if xi <= 0:
+        return out
+    rank_of, local_of = part["rank_of"], part["local_of"]
+    for pr in net.projections:
+        if expected_per_source(pr) < xi:
+            continue
+        srcs = pr.src_first + pr.src_stride * np.arange(pr.n_src)
+        tgts = pr.tgt_first + pr.tgt_stride * np.arange(pr.n_tgt)
+        for tau in np.unique(rank_of[tgts]):
+            for g in srcs:
+                if rank_of[g] != tau:
+                    out[int(tau)].add((int(rank_of[g]), int(local_of[g])))
+    return out
+
+
+def build_rank(syn, part, tau: int, forced=()):
     """Connections of rank tau, sorted by (local-first source rank, source, delay),
     ties in generation order.  Returns dict with row_ptr (M_tau + n_img + 1), tgt
     (local target index), d, w, src (global), gidx, img_sigma / img_s per image row
-    and the R / L maps per source rank."""
+    and the R / L maps per source rank.  ``forced`` adds images (sigma, s) without
+    connections (the all-sources variant); their rows are empty."""
     R, M = part["R"], part["M"]
     rank_of, local_of = part["rank_of"], part["local_of"]
     sel = np.nonzero(rank_of[syn["tgt"]] == tau)[0]
@@ -85,6 +122,13 @@ def build_rank(syn, part, tau: int):
     else:
         img_counts = np.zeros(0, np.int64)
         img_sigma = img_s = np.zeros(0, np.int64)
+    if forced:
+        # union with the forced images, in (sigma, s) order; forced-only rows are empty
+        have = dict(zip(zip(img_sigma.tolist(), img_s.tolist()), img_counts.tolist()))
+        keys = sorted(set(have) | set(forced))
+        img_sigma = np.array([k[0] for k in keys], dtype=np.int64)
+        img_s = np.array([k[1] for k in keys], dtype=np.int64)
+        img_counts = np.array([have.get(k, 0) for k in keys], dtype=np.int64)
     row_ptr = np.concatenate([[0], np.cumsum(np.concatenate([local_counts, img_counts]))]).astype(np.int64)
     maps_R, maps_L = {}, {}
     for sig in range(R):
@@ -99,9 +143,10 @@ def build_rank(syn, part, tau: int):
                 img_s=img_s.astype(np.int64), R=maps_R, L=maps_L, M=M[tau])
 
 
-def source_sequences(syn, part, sigma: int):
+def source_sequences(syn, part, sigma: int, forced=None):
     """Source side: S_{tau,sigma} for every tau != sigma, from the sources of the
-    connections whose source lives on sigma (no access to tau's maps)."""
+    connections whose source lives on sigma (no access to tau's maps), plus the forced
+    images of the all-sources variant (known on sigma from the projection alone)."""
     rank_of, local_of = part["rank_of"], part["local_of"]
     src, tgt = syn["src"], syn["tgt"]
     mine = rank_of[src] == sigma
@@ -110,7 +155,9 @@ def source_sequences(syn, part, sigma: int):
         if tau == sigma:
             continue
         m = mine & (rank_of[tgt] == tau)
-        out[tau] = np.unique(local_of[src[m]]).astype(np.int64)
+        used = local_of[src[m]]
+        extra = [s for (sg, s) in (forced or {}).get(tau, ()) if sg == sigma]
+        out[tau] = np.unique(np.concatenate([used, np.array(extra, dtype=np.int64)])).astype(np.int64)
     return out
 
 
@@ -159,11 +206,13 @@ def gq_tables(H, M_sigma: int):
     return ptr, np.zeros(len(H), np.int64), np.arange(len(H), dtype=np.int64)
 
 
-def build_all(syn, part):
-    """Every rank's layout and every map."""
+def build_all(syn, part, forced=None):
+    """Every rank's layout and every map (``forced``: the all-sources images per rank,
+    see forced_images)."""
     R, M = part["R"], part["M"]
-    ranks = [build_rank(syn, part, tau) for tau in range(R)]
-    S = [source_sequences(syn, part, sig) for sig in range(R)]
+    forced = forced or {t: set() for t in range(R)}
+    ranks = [build_rank(syn, part, tau, forced.get(tau, ())) for tau in range(R)]
+    S = [source_sequences(syn, part, sig, forced) for sig in range(R)]
     TP = [tp_tables(S[sig], M[sig], R, sig) for sig in range(R)]
     H = [host_array(S[sig], R, sig) for sig in range(R)]
     I = {}

@@ -262,6 +262,33 @@ def multi_area(seed: int = 1234, n_areas: int = 32, area_mean: float = 31250.0,
     return Network(f"multi_area_{total}", pops, projs, drives, n_ranks=n_ranks)
 
 
+def mixed_rules(n_ranks: int = 1, seed: int = 5, drive_rate_hz: float = 16000.0) -> Network:
+    """Four populations (A, B, D excitatory; C inhibitory) joined by projections of every
+    rule, with expected connections per source on both sides of 1: A->B fixed in-degree
+    K = 4 (3.0 per source), B->C K = 1 (0.4), C->A fixed total 200 (1.67), D->A 30
+    (0.33), A->C pairwise Bernoulli p = 0.02 (2.4), B->D by geometric gaps p = 0.005
+    (0.45), C->B by geometric gaps p = 0.05 (15), and A's even neurons -> D with
+    K = 2 (0.9, a strided source set).  The workload of the all-sources image threshold
+    xi: at xi = 1 four projections take all-sources images and four flag used sources."""
+    pops = [Population(400, BALANCED_PARAMS, "A"), Population(300, BALANCED_PARAMS, "B"),
+            Population(120, BALANCED_PARAMS, "C"), Population(90, BALANCED_PARAMS, "D")]
+    a, b, c, d = 0, 400, 700, 820
+    w_e = Dist(W_NORMAL_SIGN, J_E, 0.1 * J_E)
+    w_i = Dist(W_NORMAL_SIGN, -G_INH * J_E, 0.1 * G_INH * J_E)
+    projs = [
+        Projection(a, 400, b, 300, Rule(RULE_FIXED_INDEGREE, 4), w_e, DELAY_NORMAL, seed),
+        Projection(b, 300, c, 120, Rule(RULE_FIXED_INDEGREE, 1), w_e, DELAY_NORMAL, seed),
+        Projection(c, 120, a, 400, Rule(RULE_FIXED_TOTAL, 200), w_i, DELAY_NORMAL, seed),
+        Projection(d, 90, a, 400, Rule(RULE_FIXED_TOTAL, 30), w_e, DELAY_NORMAL, seed),
+        Projection(a, 400, c, 120, Rule(RULE_PAIRWISE_BERNOULLI, 0.02), w_e, DELAY_NORMAL, seed),
+        Projection(b, 300, d, 90, Rule(RULE_PAIRWISE_BERNOULLI_GEOMETRIC, 0.005), w_e, DELAY_NORMAL, seed),
+        Projection(c, 120, b, 300, Rule(RULE_PAIRWISE_BERNOULLI_GEOMETRIC, 0.05), w_i, DELAY_NORMAL, seed),
+        Projection(a, 200, d, 90, Rule(RULE_FIXED_INDEGREE, 2), w_e, DELAY_NORMAL, seed, src_stride=2),
+    ]
+    drives = [Drive(0, 910, drive_rate_hz, J_E, seed)]
+    return Network("mixed_rules", pops, projs, drives, n_ranks=n_ranks)
+
+
 def tiny(rule: str, param: float, n_src: int = 20, n_tgt: int = 20, *, seed: int = 7,
          delay: Dist = Dist(D_NORMAL_MIN, 0.5, 0.3, 0.1), n_ranks: int = 1,
          weight: Dist = Dist(W_NORMAL_SIGN, 50.0, 10.0)) -> Network:

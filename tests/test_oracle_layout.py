@@ -3,6 +3,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 from oracle import connect as oc
 from oracle import layout as ol
@@ -141,3 +142,104 @@ def test_image_rows_hold_remote_connections():
             assert np.all(rk["src"][a:b] == s * 3 + sig)
         a, b = rk["row_ptr"][0], rk["row_ptr"][M]
         assert np.all(rk["src"][a:b] % 3 == tau)
+
+
+# ---- all-sources images (threshold xi, Methods "Remote connections") ----
+
+def test_xi_quantity_is_the_mean_connections_per_source():
+    """The per-projection quantity compared with xi is the expected number of outgoing
+    connections of a source: exactly the generated count / n_src for the fixed rules,
+    within 5 sigma of the binomial mean for pairwise Bernoulli."""
+    net = wl.mixed_rules(seed=5)
+    syn = oc.generate(net)
+    for pid, pr in enumerate(net.projections):
+        n = int(np.sum(syn["proj"] == pid))
+        e = ol.expected_per_source(pr)
+        if pr.rule.kind in (wl.RULE_FIXED_INDEGREE, wl.RULE_FIXED_TOTAL):
+            assert n == e * pr.n_src
+        else:
+            pairs = pr.n_src * pr.n_tgt
+            sd = np.sqrt(pairs * pr.rule.param * (1 - pr.rule.param))
+            assert abs(n - e * pr.n_src) <= 5 * sd + 1
+    got = [ol.expected_per_source(pr) >= 1.0 for pr in net.projections]
+    assert got == [True, False, True, False, True, False, True, False]
+
+
+def _images(rk):
+    return set(zip(rk["img_sigma"].tolist(), rk["img_s"].tolist()))
+
+
+@pytest.mark.parametrize("R", [3, 8])
+def test_all_sources_images_extend_the_flagged_ones(R):
+    """xi = 1: the images on tau are the used sources plus every source of a projection
+    reaching xi that has a target on tau (brute force over the gids); extra images have
+    empty rows, the connections themselves are unchanged, S stays aligned with R."""
+    net = wl.mixed_rules(n_ranks=R)
+    syn = oc.generate(net)
+    part = ol.round_robin(net.n_neurons, R)
+    flagged = ol.build_all(syn, part)
+    forced = ol.forced_images(net, part, 1.0)
+    full = ol.build_all(syn, part, forced)
+    for tau in range(R):
+        a, b = flagged["ranks"][tau], full["ranks"][tau]
+        for k in ("tgt", "d", "w", "src", "gidx"):
+            np.testing.assert_array_equal(a[k], b[k])
+        used = _images(a)
+        want = set(used)
+        for pr in net.projections:
+            if ol.expected_per_source(pr) < 1.0:
+                continue
+            tg = pr.tgt_first + pr.tgt_stride * np.arange(pr.n_tgt)
+            if not np.any(tg % R == tau):
+                continue
+            for g in (pr.src_first + pr.src_stride * np.arange(pr.n_src)).tolist():
+                if g % R != tau:
+                    want.add((g % R, g // R))
+        assert _images(b) == want and len(want) > len(used)
+        M = b["M"]
+        for i, key in enumerate(zip(b["img_sigma"].tolist(), b["img_s"].tolist())):
+            n = b["row_ptr"][M + i + 1] - b["row_ptr"][M + i]
+            assert (n > 0) == (key in used)
+        for sig in range(R):
+            if sig != tau:
+                np.testing.assert_array_equal(full["S"][sig][tau], b["R"][sig])    # Eq. mapalign
+                assert np.all(np.diff(b["R"][sig]) > 0)                            # Eq. sortedmaps
+
+
+def test_all_sources_images_closed_form():
+    """One fixed in-degree projection S -> T with K = 1 over 1,000 + 1,000 neurons on 8
+    ranks: at xi = 1 every rank holds an image of every source on another rank
+    (1000 - 125 images), at xi = 1.5 only of the sources it uses."""
+    pops = [wl.Population(1000), wl.Population(1000)]
+    pr = wl.Projection(0, 1000, 1000, 1000, wl.Rule(wl.RULE_FIXED_INDEGREE, 1), wl.Dist(wl.W_CONST, 1.0),
+                       wl.Dist(wl.D_CONST, 1.0), 9)
+    net = wl.Network("k1", pops, [pr], n_ranks=8)
+    syn = oc.generate(net)
+    part = ol.round_robin(net.n_neurons, 8)
+    at1 = ol.build_all(syn, part, ol.forced_images(net, part, 1.0))
+    at15 = ol.build_all(syn, part, ol.forced_images(net, part, 1.5))
+    for tau in range(8):
+        assert len(at1["ranks"][tau]["img_s"]) == 1000 - 125
+        used = np.unique(syn["src"][(syn["tgt"] % 8 == tau) & (syn["src"] % 8 != tau)])
+        assert len(at15["ranks"][tau]["img_s"]) == len(used) < 1000 - 125
+
+
+def test_xi_off_is_the_flagged_layout():
+    net = wl.mixed_rules(n_ranks=4)
+    part = ol.round_robin(net.n_neurons, 4)
+    for xi in (0.0, -1.0, 1e9):
+        assert all(not v for v in ol.forced_images(net, part, xi).values())
+
+
+def test_all_sources_images_only_on_ranks_with_targets():
+    """Targets 1003, 1011, ... (stride 8 on 8 ranks) all live on rank 3: K = 8 over 125
+    targets is 1 connection per source, so rank 3 holds 875 images and no other rank
+    holds any."""
+    pops = [wl.Population(1000), wl.Population(1000)]
+    pr = wl.Projection(0, 1000, 1003, 125, wl.Rule(wl.RULE_FIXED_INDEGREE, 8), wl.Dist(wl.W_CONST, 1.0),
+                       wl.Dist(wl.D_CONST, 1.0), 9, tgt_stride=8)
+    net = wl.Network("k8_rank3", pops, [pr], n_ranks=8)
+    syn = oc.generate(net)
+    part = ol.round_robin(net.n_neurons, 8)
+    out = ol.build_all(syn, part, ol.forced_images(net, part, 1.0))
+    assert [len(r["img_s"]) for r in out["ranks"]] == [0, 0, 0, 875, 0, 0, 0, 0]
