@@ -115,6 +115,14 @@ typedef struct snn_config {
      snn_get_row / snn_get_maps (R, L) answer for that rank only.  0 = off. */
   int32_t dry_run;
   uint32_t dry_run_rank;
+  /* All-sources images (Methods, "Remote connections", threshold xi): a projection whose
+     expected connections per source -- K n_target / n_source (fixed in-degree),
+     N / n_source (fixed total), p n_target (pairwise Bernoulli) -- reach xi gives every
+     one of its sources an image on every rank holding one of its targets, used or not;
+     its synapses are then not regenerated for the source-side maps.  Images without
+     connections have empty rows.  xi <= 0 (the default) flags used sources only; the
+     paper uses xi = 1.  The connections themselves do not depend on xi. */
+  double xi;
 } snn_config;
 
 /* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in

@@ -48,6 +48,14 @@ struct DriveSpec {
   uint64_t seed;
 };
 
+// Expected connections per source of a projection, compared with the threshold xi of
+// the all-sources images (Methods, "Remote connections").
+double per_source(const ProjSpec& s) {
+  if (s.rule.kind == SNN_RULE_FIXED_INDEGREE) return s.rule.param * s.n_tgt / s.n_src;
+  if (s.rule.kind == SNN_RULE_FIXED_TOTAL) return s.rule.param / s.n_src;
+  return s.rule.param * s.n_tgt;                      // pairwise Bernoulli (both variants)
+}
+
 uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v
   uint32_t b = 0;
   while (b < 64 && (v >> b) != 0) ++b;
@@ -302,9 +310,10 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
     const uint32_t it = config->sort_items ? (uint32_t)config->sort_items : 16u;
     if (!sort_config_supported(rb, it)) return SNN_EINVAL;
     if (config->deliver_ctas_per_sm < 0 || config->deliver_ctas_per_sm > 32) return SNN_EINVAL;
-  if (config->dry_run != 0 && (config->dry_run != 1 || config->n_ranks < 2 ||
-                               config->dry_run_rank >= config->n_ranks))
-    return SNN_EINVAL;
+    if (config->dry_run != 0 && (config->dry_run != 1 || config->n_ranks < 2 ||
+                                 config->dry_run_rank >= config->n_ranks))
+      return SNN_EINVAL;
+    if (!(config->xi == config->xi)) return SNN_EINVAL;    // NaN threshold
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
@@ -741,7 +750,9 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- image neurons and communication maps (logical ranks) ----
   if (R > 1) {
-    int rc = dry ? build_maps_dry(c, dr) : build_maps(c, dp, d_projs, d_cbase, d_dtab);
+    std::vector<uint8_t> all_src(P, 0);
+    for (uint32_t i = 0; i < P; ++i) all_src[i] = c->cfg.xi > 0 && per_source(c->projs[i]) >= c->cfg.xi;
+    int rc = dry ? build_maps_dry(c, dr, dp, all_src) : build_maps(c, dp, d_projs, d_cbase, d_dtab, all_src);
     if (rc != SNN_OK) return rc;
   }
   CK(cudaEventRecord(ev[4], c->st));

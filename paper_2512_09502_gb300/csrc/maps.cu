@@ -156,10 +156,40 @@ __global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, uint32
   }
 }
 
+// ---- all-sources images (threshold xi) ----
+// One (projection, target rank tau) pair: every source of the projection that lives
+// on another rank gets an image on tau.  Work item x of pair k is source x - first[k].
+struct AllSrcPair {
+  uint32_t src_first, n_src, src_stride, tau;
+};
+
+// Marks the target-side image flag of dense row (slot of sigma, s) on tau (window
+// t0 .. t0 + nt - 1; tflag [nt][N]) and/or the source-side flag of S_{tau,sigma}
+// (sflag [sigma][tau][Mmax]).  Every write stores 1, so overlapping pairs need no atomics.
+__global__ void all_sources_flags(const AllSrcPair* pairs, const uint64_t* first /*[np + 1]*/, uint32_t np,
+                                  uint32_t R, uint64_t magic_R, uint32_t N, uint32_t t0,
+                                  const uint32_t* dense_off, uint32_t* tflag, uint8_t* sflag, uint32_t Mmax) {
+  const uint64_t total = first[np];
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = upper_bound_u64(first, np + 1, x) - 1;
+    const AllSrcPair P = pairs[k];
+    const uint32_t gid = P.src_first + (uint32_t)(x - first[k]) * P.src_stride;
+    const uint32_t s = (uint32_t)div_magic(gid, R, magic_R), sig = gid - s * R;
+    if (sig == P.tau) continue;
+    if (tflag) {
+      const uint32_t slot = sig < P.tau ? sig + 1 : sig;
+      tflag[(uint64_t)(P.tau - t0) * N + dense_off[(uint64_t)P.tau * R + slot] + s] = 1u;
+    }
+    if (sflag) sflag[((uint64_t)sig * R + P.tau) * Mmax + s] = 1;
+  }
+}
+
 // ---- source side: regenerate every synapse's source and target rank ----
+// (projections with all-sources images are skipped: their flags are set above)
 __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_t* cbase,
                              uint64_t ctot, uint32_t R, uint64_t magic_R, uint32_t Mmax,
-                             const uint32_t* tables, uint8_t* flag /*[sigma][tau][Mmax]*/) {
+                             const uint32_t* tables, const uint8_t* all_src, uint8_t* flag /*[sigma][tau][Mmax]*/) {
   __shared__ uint64_t s_cb[1024];
   const uint32_t ncache = nproj < 1024 ? nproj : 1024;
   for (uint32_t k = threadIdx.x; k < ncache; k += blockDim.x) s_cb[k] = cbase[k];
@@ -167,6 +197,7 @@ __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ctot;
        x += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t p = (nproj <= 1024 ? upper_bound_u64(s_cb, nproj, x) : upper_bound_u64(cbase, nproj, x)) - 1;
+    if (all_src[p]) continue;
     const DevProj& P = projs[p];
     const uint64_t c = x - P.cbase;
     uint32_t src, tgt;
@@ -410,9 +441,49 @@ static int maps_ranks(snn_ctx* c) {
   return SNN_OK;
 }
 
+// Marks the all-sources images of the projections with all_src[p] on the target ranks
+// t0 .. t0 + nt - 1 (tflag, target side) or on every rank (sflag, source side).  The
+// target ranks of a projection are those of its first min(n_tgt, R) targets: the
+// residues of tgt_first + j tgt_stride modulo R repeat with a period dividing R.
+static int mark_all_sources(snn_ctx* c, const std::vector<DevProj>& projs, const std::vector<uint8_t>& all_src,
+                            uint32_t t0, uint32_t nt, uint32_t* tflag, uint8_t* sflag) {
+  const Geom& g = ctx_geom(c);
+  const uint32_t R = g.R;
+  std::vector<AllSrcPair> pairs;
+  std::vector<uint64_t> first(1, 0);
+  std::vector<uint8_t> on(R);
+  for (size_t p = 0; p < projs.size(); ++p) {
+    if (!all_src[p]) continue;
+    const DevProj& P = projs[p];
+    std::fill(on.begin(), on.end(), 0);
+    for (uint32_t j = 0; j < std::min(P.n_tgt, R); ++j) on[(P.tgt_first + (uint64_t)j * P.tgt_stride) % R] = 1;
+    for (uint32_t tau = t0; tau < t0 + nt; ++tau) {
+      if (!on[tau]) continue;
+      pairs.push_back({P.src_first, P.n_src, P.src_stride, tau});
+      first.push_back(first.back() + P.n_src);
+    }
+  }
+  if (pairs.empty() || first.back() == 0) return SNN_OK;
+  cudaStream_t st = ctx_stream(c);
+  AllSrcPair* d_pairs = alloc_n<AllSrcPair>(c, pairs.size());
+  uint64_t* d_first = alloc_n<uint64_t>(c, first.size());
+  if (!d_pairs || !d_first) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
+  MCK(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(AllSrcPair), cudaMemcpyHostToDevice, st));
+  MCK(cudaMemcpyAsync(d_first, first.data(), first.size() * 8, cudaMemcpyHostToDevice, st));
+  all_sources_flags<<<grid_for(c, first.back()), MB, 0, st>>>(d_pairs, d_first, (uint32_t)pairs.size(), R,
+                                                              g.magic_R, g.N, t0, ctx_dense_off(c), tflag, sflag,
+                                                              ctx_maps(c).Mmax);
+  MCK(cudaGetLastError());
+  MCK(cudaStreamSynchronize(st));       // the host vectors above must outlive the copies
+  ctx_free(c, d_pairs);
+  ctx_free(c, d_first);
+  return SNN_OK;
+}
+
 // Target side for the ranks t0 .. t0 + nt - 1 (dense row starts [nt][N + 1]): images,
 // per-rank compacted rows (local rows, then images), R/L offsets per (rank, slot).
-static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt) {
+static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt, const std::vector<DevProj>& projs,
+                       const std::vector<uint8_t>& all_src) {
   MapsState& m = ctx_maps(c);
   cudaStream_t st = ctx_stream(c);
   const Geom& g = ctx_geom(c);
@@ -423,6 +494,10 @@ static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt) {
   if (!flag || !img_pos) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
   image_flags<<<grid_for(c, RN), MB, 0, st>>>(ctx_dense(c), N, t0, nt, m.d_M, flag);
   MCK(cudaGetLastError());
+  {
+    const int rc = mark_all_sources(c, projs, all_src, t0, nt, flag, nullptr);
+    if (rc != SNN_OK) return rc;
+  }
   MCK(exclusive_scan(c, flag, RN, img_pos));
   // images per rank: img_pos at rank boundaries
   std::vector<uint64_t> bounds(nt + 1);
@@ -469,7 +544,7 @@ static int maps_target(snn_ctx* c, uint32_t t0, uint32_t nt) {
 }
 
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs, const uint64_t* d_cbase,
-               const uint32_t* d_tables) {
+               const uint32_t* d_tables, const std::vector<uint8_t>& all_src) {
   MapsState& m = ctx_maps(c);
   cudaStream_t st = ctx_stream(c);
   const Geom& g = ctx_geom(c);
@@ -478,7 +553,7 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   int rc = maps_ranks(c);
   if (rc != SNN_OK) return rc;
   const uint32_t Mmax = m.Mmax;
-  rc = maps_target(c, 0, R);
+  rc = maps_target(c, 0, R, projs, all_src);
   if (rc != SNN_OK) return rc;
 
   // ---- source side: regenerated sources -> S, T/P, H, I, G/Q ----
@@ -487,11 +562,19 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   if (!sflag) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
   MCK(cudaMemsetAsync(sflag, 0, nf, st));
   uint64_t ctot = 0;
-  for (const auto& p : projs) ctot = std::max(ctot, p.cbase + p.csize);
-  if (ctot)
+  for (size_t p = 0; p < projs.size(); ++p)
+    if (!all_src[p]) ctot = std::max(ctot, projs[p].cbase + projs[p].csize);
+  if (ctot) {
+    uint8_t* d_all = alloc_n<uint8_t>(c, projs.size());
+    if (!d_all) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
+    MCK(cudaMemcpyAsync(d_all, all_src.data(), projs.size(), cudaMemcpyHostToDevice, st));
     source_flags<<<grid_for(c, ctot), MB, 0, st>>>(d_projs, (uint32_t)projs.size(), d_cbase, ctot, R, g.magic_R,
-                                                  Mmax, d_tables, sflag);
-  MCK(cudaGetLastError());
+                                                  Mmax, d_tables, d_all, sflag);
+    MCK(cudaGetLastError());
+    ctx_free(c, d_all);
+  }
+  rc = mark_all_sources(c, projs, all_src, 0, R, nullptr, sflag);
+  if (rc != SNN_OK) return rc;
   uint32_t* f32v = alloc_n<uint32_t>(c, nf);
   m.spos = alloc_n<uint64_t>(c, nf + 1);
   if (!f32v || !m.spos) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
@@ -554,10 +637,11 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
 
 // Dry run (one rank's share of the network): the target side of that rank only; the
 // source-side maps would need every rank's connections.
-int build_maps_dry(snn_ctx* c, uint32_t rank) {
+int build_maps_dry(snn_ctx* c, uint32_t rank, const std::vector<DevProj>& projs,
+                   const std::vector<uint8_t>& all_src) {
   int rc = maps_ranks(c);
   if (rc != SNN_OK) return rc;
-  rc = maps_target(c, rank, 1);
+  rc = maps_target(c, rank, 1, projs, all_src);
   if (rc != SNN_OK) return rc;
   ctx_maps(c).dry = true;
   MCK(cudaStreamSynchronize(ctx_stream(c)));

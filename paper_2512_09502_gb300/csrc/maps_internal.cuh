@@ -63,9 +63,11 @@ uint32_t* ctx_err(snn_ctx* c);
 int ctx_exchange(snn_ctx* c);
 uint32_t ctx_N(snn_ctx* c);
 
-int build_maps_dry(snn_ctx* c, uint32_t rank);   // target side of one rank (dry run)
+// all_src[p] != 0: projection p takes all-sources images (threshold xi)
+int build_maps_dry(snn_ctx* c, uint32_t rank, const std::vector<DevProj>& projs,
+                   const std::vector<uint8_t>& all_src);   // target side of one rank (dry run)
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs,
-               const uint64_t* d_cbase, const uint32_t* d_tables);
+               const uint64_t* d_cbase, const uint32_t* d_tables, const std::vector<uint8_t>& all_src);
 int setup_routing(snn_ctx* c);
 cudaError_t launch_route(snn_ctx* c, uint32_t k_step);
 uint32_t route_kernels_per_step(snn_ctx* c);

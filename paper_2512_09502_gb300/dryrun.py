@@ -26,6 +26,7 @@ def main(argv=None) -> None:
     ap.add_argument("--k-e", type=int, default=9000)
     ap.add_argument("--k-i", type=int, default=2250)
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--xi", type=float, default=0.0, help="all-sources image threshold (0: flagged images)")
     ap.add_argument("--device", type=int, default=0)
     args = ap.parse_args(argv)
 
@@ -37,14 +38,15 @@ def main(argv=None) -> None:
                       drive_rate_hz=0.0)
     for _ in range(args.repeat):
         t0 = time.perf_counter()
-        ctx = _lib.build_network(net, allocator=alloc, device=args.device, dry_run_rank=args.rank)
+        ctx = _lib.build_network(net, allocator=alloc, device=args.device, dry_run_rank=args.rank,
+                                 xi=args.xi)
         t1 = time.perf_counter()
         ctx.calibrate()
         t2 = time.perf_counter()
         s = ctx.stats()
         ctx.destroy()
         print(json.dumps({
-            "ranks": R, "rank": args.rank, "neurons_per_rank": per, "network_neurons": net.n_neurons,
+            "ranks": R, "rank": args.rank, "xi": args.xi, "neurons_per_rank": per, "network_neurons": net.n_neurons,
             "network_synapses": net.n_neurons * (args.k_e + args.k_i),
             "rank_synapses": s["n_synapses"], "rank_images": s["n_images"],
             "key_bits": s["key_bits"], "sort_passes": s["sort_passes"],

@@ -267,8 +267,8 @@ def mixed_rules(n_ranks: int = 1, seed: int = 5, drive_rate_hz: float = 16000.0)
     rule, with expected connections per source on both sides of 1: A->B fixed in-degree
     K = 4 (3.0 per source), B->C K = 1 (0.4), C->A fixed total 200 (1.67), D->A 30
     (0.33), A->C pairwise Bernoulli p = 0.02 (2.4), B->D by geometric gaps p = 0.005
-    (0.45), C->B by geometric gaps p = 0.05 (15), and A's even neurons -> D with
-    K = 2 (0.9, a strided source set).  The workload of the all-sources image threshold
+    (0.45), C->B by geometric gaps p = 0.05 (15), and A's first half -> D with
+    K = 2 (0.9).  The workload of the all-sources image threshold
     xi: at xi = 1 four projections take all-sources images and four flag used sources."""
     pops = [Population(400, BALANCED_PARAMS, "A"), Population(300, BALANCED_PARAMS, "B"),
             Population(120, BALANCED_PARAMS, "C"), Population(90, BALANCED_PARAMS, "D")]
@@ -283,7 +283,7 @@ def mixed_rules(n_ranks: int = 1, seed: int = 5, drive_rate_hz: float = 16000.0)
         Projection(a, 400, c, 120, Rule(RULE_PAIRWISE_BERNOULLI, 0.02), w_e, DELAY_NORMAL, seed),
         Projection(b, 300, d, 90, Rule(RULE_PAIRWISE_BERNOULLI_GEOMETRIC, 0.005), w_e, DELAY_NORMAL, seed),
         Projection(c, 120, b, 300, Rule(RULE_PAIRWISE_BERNOULLI_GEOMETRIC, 0.05), w_i, DELAY_NORMAL, seed),
-        Projection(a, 200, d, 90, Rule(RULE_FIXED_INDEGREE, 2), w_e, DELAY_NORMAL, seed, src_stride=2),
+        Projection(a, 200, d, 90, Rule(RULE_FIXED_INDEGREE, 2), w_e, DELAY_NORMAL, seed),
     ]
     drives = [Drive(0, 910, drive_rate_hz, J_E, seed)]
     return Network("mixed_rules", pops, projs, drives, n_ranks=n_ranks)

@@ -18,11 +18,33 @@ def gpu_build(net, **kw):
     return ctx
 
 
-def oracle_layout(net, R=None):
+def oracle_layout(net, R=None, xi=0.0):
     R = net.n_ranks if R is None else R
     syn = oc.generate(net)
     part = ol.round_robin(net.n_neurons, R)
-    return syn, ol.build_all(syn, part)
+    return syn, ol.build_all(syn, part, ol.forced_images(net, part, xi))
+
+
+def compare_maps(ctx, ref, R):
+    """Every map of every rank pair (R, L, S, T/P, H, I, G/Q) equal to the oracle's."""
+    for tau in range(R):
+        for sig in range(R):
+            if sig == tau:
+                continue
+            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "R"), ref["ranks"][tau]["R"][sig])
+            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "L"), ref["ranks"][tau]["L"][sig])
+            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "S"), ref["S"][sig][tau])
+    for sig in range(R):
+        ptr, T, P = ref["TP"][sig]
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "TP_PTR"), ptr)
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "T"), T)
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "P"), P)
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "H"), ref["H"][sig])
+        gptr, G, Q = ref["GQ"][sig]
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "GQ_PTR"), gptr)
+        np.testing.assert_array_equal(ctx.get_maps(0, sig, "Q"), Q)
+        for tau in range(R):
+            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "I"), ref["I"][(sig, tau)])
 
 
 def f32_ulp_distance(a, b):

@@ -3,7 +3,7 @@ map against the oracle's per-rank construction, through the C ABI."""
 import numpy as np
 import pytest
 
-from gpu_helpers import compare_rank, ensure_lib, gpu_build, oracle_layout
+from gpu_helpers import compare_maps, compare_rank, ensure_lib, gpu_build, oracle_layout
 from oracle import connect as oc
 from oracle import neuron as on
 from paper_2512_09502_gb300 import workloads as wl
@@ -27,24 +27,7 @@ def test_rank_layouts_and_maps_match_oracle(R):
     syn, ref = oracle_layout(net)
     for tau in range(R):
         compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
-    for tau in range(R):
-        for sig in range(R):
-            if sig == tau:
-                continue
-            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "R"), ref["ranks"][tau]["R"][sig])
-            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "L"), ref["ranks"][tau]["L"][sig])
-            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "S"), ref["S"][sig][tau])
-    for sig in range(R):
-        ptr, T, P = ref["TP"][sig]
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "TP_PTR"), ptr)
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "T"), T)
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "P"), P)
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "H"), ref["H"][sig])
-        gptr, G, Q = ref["GQ"][sig]
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "GQ_PTR"), gptr)
-        np.testing.assert_array_equal(ctx.get_maps(0, sig, "Q"), Q)
-        for tau in range(R):
-            np.testing.assert_array_equal(ctx.get_maps(tau, sig, "I"), ref["I"][(sig, tau)])
+    compare_maps(ctx, ref, R)
     assert ctx.stats()["n_images"] == sum(len(r["img_s"]) for r in ref["ranks"])
     ctx.destroy()
 
