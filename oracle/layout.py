@@ -11,9 +11,9 @@ Definitions followed (paper, Methods, "Remote connections"):
   "Point-to-point MPI communication").  Only sources with at least one connection into
   tau get an image (the flagged variant of RemoteConnect, used for randomly drawn
   sources).
-* With the paper's threshold xi (Methods, "Remote connections") a projection whose
-  expected connections per source reach xi skips the flagging: all its sources get an
-  image on every rank holding its targets (``forced_images``); xi <= 0 keeps flagging.
+* With the paper's threshold xi (Methods, "Remote connections"), where a projection's
+  expected connections per source on rank tau reach xi, the flagging is skipped there:
+  all its sources get an image on tau (``forced_images``); xi <= 0 keeps flagging.
 * Connections are sorted by source as the first key so that one source's outgoing
   connections are (first index, count) ("GPU memory levels"); the second key is the
   delay, and ties keep generation order (reading: stable sort, tie-break gidx).
@@ -62,36 +62,41 @@ def source_slot(sigma, tau):
     return np.where(sigma == tau, 0, np.where(sigma < tau, sigma + 1, sigma))
 
 
-def expected_per_source(pr) -> float:
-    """Expected connections per source of a projection, the quantity the paper's xi
+def expected_per_source(pr, n_tgt_on=None) -> float:
+    """Expected connections per source that a projection creates on one rank holding
+    ``n_tgt_on`` of its targets (default: all of them), the ratio the paper's xi
     heuristic compares (Methods, "Remote connections": K_in N_target / N_source for the
-    fixed in-degree rule)."""
+    fixed in-degree rule, N_target the targets on the target process): K n_on / n_src
+    (fixed in-degree), N n_on / (n_tgt n_src) (fixed total, N spread uniformly over
+    the targets), p n_on (pairwise Bernoulli)."""
+    n_on = pr.n_tgt if n_tgt_on is None else int(n_tgt_on)
     if pr.rule.kind == "fixed_indegree":
-        return pr.rule.param * pr.n_tgt / pr.n_src
+        return pr.rule.param * n_on / pr.n_src
     if pr.rule.kind == "fixed_total":
-        return pr.rule.param / pr.n_src
-    return pr.rule.param * pr.n_tgt                     # pairwise Bernoulli (both variants)
+        return pr.rule.param * n_on / (pr.n_tgt * pr.n_src)
+    return pr.rule.param * n_on                        # pairwise Bernoulli (both variants)
 
 
 def forced_images(net, part, xi: float):
-    """All-sources variant (xi > 0): a projection whose expected connections per source
-    reach xi gives every one of its sources an image on every rank holding one of its
-    targets, whether or not the source is used there.  Returns {tau: set of (sigma, s)}
-    with sigma != tau; empty sets for xi <= 0 (flagged images only)."""
+    """All-sources variant (xi > 0): where a projection's expected connections per source
+    on rank tau reach xi, every one of its sources on another rank gets an image on tau,
+    whether or not it is used there.  Returns {tau: set of (sigma, s)}; empty sets for
+    xi <= 0 (flagged images only)."""
     R = part["R"]
     out = {t: set() for t in range(R)}
     if xi <= 0:
         return out
     rank_of, local_of = part["rank_of"], part["local_of"]
     for pr in net.projections:
-        if expected_per_source(pr) < xi:
-            continue
         srcs = pr.src_first + pr.src_stride * np.arange(pr.n_src)
         tgts = pr.tgt_first + pr.tgt_stride * np.arange(pr.n_tgt)
-        for tau in np.unique(rank_of[tgts]):
+        n_on = np.bincount(rank_of[tgts], minlength=R)
+        for tau in range(R):
+            if n_on[tau] == 0 or expected_per_source(pr, n_on[tau]) < xi:
+                continue
             for g in srcs:
                 if rank_of[g] != tau:
-                    out[int(tau)].add((int(rank_of[g]), int(local_of[g])))
+                    out[tau].add((int(rank_of[g]), int(local_of[g])))
     return out
 
 

@@ -48,12 +48,33 @@ struct DriveSpec {
   uint64_t seed;
 };
 
-// Expected connections per source of a projection, compared with the threshold xi of
-// the all-sources images (Methods, "Remote connections").
-double per_source(const ProjSpec& s) {
-  if (s.rule.kind == SNN_RULE_FIXED_INDEGREE) return s.rule.param * s.n_tgt / s.n_src;
-  if (s.rule.kind == SNN_RULE_FIXED_TOTAL) return s.rule.param / s.n_src;
-  return s.rule.param * s.n_tgt;                      // pairwise Bernoulli (both variants)
+// Expected connections per source that a projection creates on a rank holding n_on of
+// its targets, compared with the threshold xi of the all-sources images (Methods,
+// "Remote connections": K_in N_target / N_source for fixed in-degree, N_target the
+// targets on the target process).
+double per_source(const ProjSpec& s, uint64_t n_on) {
+  if (s.rule.kind == SNN_RULE_FIXED_INDEGREE) return s.rule.param * (double)n_on / s.n_src;
+  if (s.rule.kind == SNN_RULE_FIXED_TOTAL) return s.rule.param * (double)n_on / ((double)s.n_tgt * s.n_src);
+  return s.rule.param * (double)n_on;                 // pairwise Bernoulli (both variants)
+}
+
+uint64_t gcd_u64(uint64_t a, uint64_t b) {
+  while (b) {
+    const uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// Targets of a projection per rank: the residues of tgt_first + j tgt_stride (mod R)
+// repeat with period q = R / gcd(tgt_stride, R), each once per period.
+void targets_per_rank(const ProjSpec& s, uint32_t R, std::vector<uint64_t>* n_on) {
+  n_on->assign(R, 0);
+  const uint64_t q = R / gcd_u64(s.tgt_stride % R, R);
+  const uint64_t a = s.n_tgt / q, b = s.n_tgt % q;
+  for (uint64_t j = 0; j < std::min<uint64_t>(s.n_tgt, q); ++j)
+    (*n_on)[(s.tgt_first + j * s.tgt_stride) % R] += a + (j < b ? 1 : 0);
 }
 
 uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v
@@ -750,8 +771,16 @@ int snn_calibrate(snn_ctx* c) {
 
   // ---- image neurons and communication maps (logical ranks) ----
   if (R > 1) {
-    std::vector<uint8_t> all_src(P, 0);
-    for (uint32_t i = 0; i < P; ++i) all_src[i] = c->cfg.xi > 0 && per_source(c->projs[i]) >= c->cfg.xi;
+    // all_src[p][tau]: projection p gives all its sources images on tau
+    std::vector<uint8_t> all_src((size_t)P * R, 0);
+    if (c->cfg.xi > 0) {
+      std::vector<uint64_t> n_on;
+      for (uint32_t i = 0; i < P; ++i) {
+        targets_per_rank(c->projs[i], R, &n_on);
+        for (uint32_t t = 0; t < R; ++t)
+          all_src[(size_t)i * R + t] = n_on[t] > 0 && per_source(c->projs[i], n_on[t]) >= c->cfg.xi;
+      }
+    }
     int rc = dry ? build_maps_dry(c, dr, dp, all_src) : build_maps(c, dp, d_projs, d_cbase, d_dtab, all_src);
     if (rc != SNN_OK) return rc;
   }

@@ -186,10 +186,11 @@ __global__ void all_sources_flags(const AllSrcPair* pairs, const uint64_t* first
 }
 
 // ---- source side: regenerate every synapse's source and target rank ----
-// (projections with all-sources images are skipped: their flags are set above)
+// (skip[p]: projection p has all-sources images on every rank holding its targets;
+// its flags are set by all_sources_flags)
 __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_t* cbase,
                              uint64_t ctot, uint32_t R, uint64_t magic_R, uint32_t Mmax,
-                             const uint32_t* tables, const uint8_t* all_src, uint8_t* flag /*[sigma][tau][Mmax]*/) {
+                             const uint32_t* tables, const uint8_t* skip, uint8_t* flag /*[sigma][tau][Mmax]*/) {
   __shared__ uint64_t s_cb[1024];
   const uint32_t ncache = nproj < 1024 ? nproj : 1024;
   for (uint32_t k = threadIdx.x; k < ncache; k += blockDim.x) s_cb[k] = cbase[k];
@@ -197,7 +198,7 @@ __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ctot;
        x += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t p = (nproj <= 1024 ? upper_bound_u64(s_cb, nproj, x) : upper_bound_u64(cbase, nproj, x)) - 1;
-    if (all_src[p]) continue;
+    if (skip[p]) continue;
     const DevProj& P = projs[p];
     const uint64_t c = x - P.cbase;
     uint32_t src, tgt;
@@ -441,24 +442,19 @@ static int maps_ranks(snn_ctx* c) {
   return SNN_OK;
 }
 
-// Marks the all-sources images of the projections with all_src[p] on the target ranks
-// t0 .. t0 + nt - 1 (tflag, target side) or on every rank (sflag, source side).  The
-// target ranks of a projection are those of its first min(n_tgt, R) targets: the
-// residues of tgt_first + j tgt_stride modulo R repeat with a period dividing R.
+// Marks the all-sources images of the pairs (p, tau) with all_src[p * R + tau] on the
+// target ranks t0 .. t0 + nt - 1 (tflag, target side) or on every rank (sflag, source
+// side).
 static int mark_all_sources(snn_ctx* c, const std::vector<DevProj>& projs, const std::vector<uint8_t>& all_src,
                             uint32_t t0, uint32_t nt, uint32_t* tflag, uint8_t* sflag) {
   const Geom& g = ctx_geom(c);
   const uint32_t R = g.R;
   std::vector<AllSrcPair> pairs;
   std::vector<uint64_t> first(1, 0);
-  std::vector<uint8_t> on(R);
   for (size_t p = 0; p < projs.size(); ++p) {
-    if (!all_src[p]) continue;
     const DevProj& P = projs[p];
-    std::fill(on.begin(), on.end(), 0);
-    for (uint32_t j = 0; j < std::min(P.n_tgt, R); ++j) on[(P.tgt_first + (uint64_t)j * P.tgt_stride) % R] = 1;
     for (uint32_t tau = t0; tau < t0 + nt; ++tau) {
-      if (!on[tau]) continue;
+      if (!all_src[p * R + tau]) continue;
       pairs.push_back({P.src_first, P.n_src, P.src_stride, tau});
       first.push_back(first.back() + P.n_src);
     }
@@ -561,17 +557,25 @@ int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_p
   uint8_t* sflag = alloc_n<uint8_t>(c, nf);
   if (!sflag) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
   MCK(cudaMemsetAsync(sflag, 0, nf, st));
+  // a projection forced on every rank holding its targets needs no regeneration: its
+  // connections only reach (sigma, s, tau) that the marking below sets anyway
+  std::vector<uint8_t> skip(projs.size(), 1);
   uint64_t ctot = 0;
-  for (size_t p = 0; p < projs.size(); ++p)
-    if (!all_src[p]) ctot = std::max(ctot, projs[p].cbase + projs[p].csize);
+  for (size_t p = 0; p < projs.size(); ++p) {
+    const DevProj& P = projs[p];
+    for (uint32_t j = 0; j < std::min(P.n_tgt, R) && skip[p]; ++j)
+      skip[p] = all_src[p * R + (P.tgt_first + (uint64_t)j * P.tgt_stride) % R];
+    if (!skip[p]) ctot = std::max(ctot, P.cbase + P.csize);
+  }
   if (ctot) {
-    uint8_t* d_all = alloc_n<uint8_t>(c, projs.size());
-    if (!d_all) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
-    MCK(cudaMemcpyAsync(d_all, all_src.data(), projs.size(), cudaMemcpyHostToDevice, st));
+    uint8_t* d_skip = alloc_n<uint8_t>(c, projs.size());
+    if (!d_skip) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
+    MCK(cudaMemcpyAsync(d_skip, skip.data(), projs.size(), cudaMemcpyHostToDevice, st));
     source_flags<<<grid_for(c, ctot), MB, 0, st>>>(d_projs, (uint32_t)projs.size(), d_cbase, ctot, R, g.magic_R,
-                                                  Mmax, d_tables, d_all, sflag);
+                                                  Mmax, d_tables, d_skip, sflag);
     MCK(cudaGetLastError());
-    ctx_free(c, d_all);
+    MCK(cudaStreamSynchronize(st));       // skip must outlive the copy
+    ctx_free(c, d_skip);
   }
   rc = mark_all_sources(c, projs, all_src, 0, R, nullptr, sflag);
   if (rc != SNN_OK) return rc;

@@ -63,7 +63,8 @@ uint32_t* ctx_err(snn_ctx* c);
 int ctx_exchange(snn_ctx* c);
 uint32_t ctx_N(snn_ctx* c);
 
-// all_src[p] != 0: projection p takes all-sources images (threshold xi)
+// all_src[p * R + tau] != 0: projection p gives all its sources images on rank tau
+// (threshold xi); set only where p has targets on tau
 int build_maps_dry(snn_ctx* c, uint32_t rank, const std::vector<DevProj>& projs,
                    const std::vector<uint8_t>& all_src);   // target side of one rank (dry run)
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs,

@@ -268,8 +268,8 @@ def mixed_rules(n_ranks: int = 1, seed: int = 5, drive_rate_hz: float = 16000.0)
     K = 4 (3.0 per source), B->C K = 1 (0.4), C->A fixed total 200 (1.67), D->A 30
     (0.33), A->C pairwise Bernoulli p = 0.02 (2.4), B->D by geometric gaps p = 0.005
     (0.45), C->B by geometric gaps p = 0.05 (15), and A's first half -> D with
-    K = 2 (0.9).  The workload of the all-sources image threshold
-    xi: at xi = 1 four projections take all-sources images and four flag used sources."""
+    K = 2 (0.9); figures per source over all targets, on R ranks about
+    1/R of them per rank.  The workload of the all-sources image threshold xi."""
     pops = [Population(400, BALANCED_PARAMS, "A"), Population(300, BALANCED_PARAMS, "B"),
             Population(120, BALANCED_PARAMS, "C"), Population(90, BALANCED_PARAMS, "D")]
     a, b, c, d = 0, 400, 700, 820

@@ -17,7 +17,7 @@ def lib():
     return ensure_lib()
 
 
-@pytest.mark.parametrize("R,xi", [(3, 1.0), (8, 1.0), (5, 0.5), (4, 0.0)])
+@pytest.mark.parametrize("R,xi", [(2, 1.0), (3, 1.0), (8, 1.0), (5, 0.5), (4, 0.0)])
 def test_all_sources_layouts_and_maps_match_oracle(R, xi):
     net = wl.mixed_rules(n_ranks=R)
     ctx = gpu_build(net, xi=xi)
@@ -74,9 +74,10 @@ def test_all_sources_images_leave_the_dynamics_unchanged(exchange):
 @pytest.mark.parametrize("r", [0, 4])
 def test_all_sources_dry_run(r):
     """A dry run with the threshold builds the rank's rows and R/L maps of the full
-    build (fixed in-degree projections only: xi = 1 forces the balanced network's)."""
+    build.  K_E = 4 over 60 targets per rank and 240 sources is exactly 1 connection per
+    source (forced at xi = 1), K_I = 1 over 61 sources is not."""
     R = 5
-    net = wl.balanced(240, 61, 3, 1, wl.DELAY_NORMAL, seed=3, n_ranks=R)
+    net = wl.balanced(240, 61, 4, 1, wl.DELAY_NORMAL, seed=3, n_ranks=R)
     full = gpu_build(net, xi=1.0)
     dry = gpu_build(net, xi=1.0, dry_run_rank=r)
     _, ref = oracle_layout(net, xi=1.0)

@@ -146,21 +146,26 @@ def test_image_rows_hold_remote_connections():
 
 # ---- all-sources images (threshold xi, Methods "Remote connections") ----
 
-def test_xi_quantity_is_the_mean_connections_per_source():
-    """The per-projection quantity compared with xi is the expected number of outgoing
-    connections of a source: exactly the generated count / n_src for the fixed rules,
-    within 5 sigma of the binomial mean for pairwise Bernoulli."""
+@pytest.mark.parametrize("R", [1, 3])
+def test_xi_quantity_is_the_mean_connections_per_source(R):
+    """The quantity compared with xi is the expected number of connections that a
+    projection creates on rank tau per source: exactly the generated count on tau / n_src
+    for fixed in-degree, within 5 sigma of the mean for fixed total and pairwise
+    Bernoulli (their counts on every rank sum to the total)."""
     net = wl.mixed_rules(seed=5)
     syn = oc.generate(net)
+    part = ol.round_robin(net.n_neurons, R)
     for pid, pr in enumerate(net.projections):
-        n = int(np.sum(syn["proj"] == pid))
-        e = ol.expected_per_source(pr)
-        if pr.rule.kind in (wl.RULE_FIXED_INDEGREE, wl.RULE_FIXED_TOTAL):
-            assert n == e * pr.n_src
-        else:
-            pairs = pr.n_src * pr.n_tgt
-            sd = np.sqrt(pairs * pr.rule.param * (1 - pr.rule.param))
-            assert abs(n - e * pr.n_src) <= 5 * sd + 1
+        mine = syn["proj"] == pid
+        tgts = pr.tgt_first + pr.tgt_stride * np.arange(pr.n_tgt)
+        n_on = np.bincount(part["rank_of"][tgts], minlength=R)
+        for tau in range(R):
+            n = int(np.sum(mine & (part["rank_of"][syn["tgt"]] == tau)))
+            e = ol.expected_per_source(pr, n_on[tau]) * pr.n_src
+            if pr.rule.kind == wl.RULE_FIXED_INDEGREE:
+                assert n == e
+            else:
+                assert abs(n - e) <= 5 * np.sqrt(e) + 1
     got = [ol.expected_per_source(pr) >= 1.0 for pr in net.projections]
     assert got == [True, False, True, False, True, False, True, False]
 
@@ -186,11 +191,12 @@ def test_all_sources_images_extend_the_flagged_ones(R):
             np.testing.assert_array_equal(a[k], b[k])
         used = _images(a)
         want = set(used)
-        for pr in net.projections:
-            if ol.expected_per_source(pr) < 1.0:
-                continue
+        for pid, pr in enumerate(net.projections):
             tg = pr.tgt_first + pr.tgt_stride * np.arange(pr.n_tgt)
-            if not np.any(tg % R == tau):
+            n_made = int(np.sum((syn["proj"] == pid) & (syn["tgt"] % R == tau)))
+            if pr.rule.kind == wl.RULE_FIXED_INDEGREE:            # exact: K per target on tau
+                assert n_made == pr.rule.param * np.sum(tg % R == tau)
+            if ol.expected_per_source(pr, np.sum(tg % R == tau)) < 1.0 or not np.any(tg % R == tau):
                 continue
             for g in (pr.src_first + pr.src_stride * np.arange(pr.n_src)).tolist():
                 if g % R != tau:
@@ -207,11 +213,12 @@ def test_all_sources_images_extend_the_flagged_ones(R):
 
 
 def test_all_sources_images_closed_form():
-    """One fixed in-degree projection S -> T with K = 1 over 1,000 + 1,000 neurons on 8
-    ranks: at xi = 1 every rank holds an image of every source on another rank
-    (1000 - 125 images), at xi = 1.5 only of the sources it uses."""
+    """One fixed in-degree projection S -> T with K = 8 over 1,000 + 1,000 neurons on 8
+    ranks (125 targets per rank: 8 x 125 / 1000 = 1 connection per source and rank): at
+    xi = 1 every rank holds an image of every source on another rank (1000 - 125
+    images), at xi = 1.5 only of the sources it uses (about 1 - 1/e of them)."""
     pops = [wl.Population(1000), wl.Population(1000)]
-    pr = wl.Projection(0, 1000, 1000, 1000, wl.Rule(wl.RULE_FIXED_INDEGREE, 1), wl.Dist(wl.W_CONST, 1.0),
+    pr = wl.Projection(0, 1000, 1000, 1000, wl.Rule(wl.RULE_FIXED_INDEGREE, 8), wl.Dist(wl.W_CONST, 1.0),
                        wl.Dist(wl.D_CONST, 1.0), 9)
     net = wl.Network("k1", pops, [pr], n_ranks=8)
     syn = oc.generate(net)
@@ -222,6 +229,7 @@ def test_all_sources_images_closed_form():
         assert len(at1["ranks"][tau]["img_s"]) == 1000 - 125
         used = np.unique(syn["src"][(syn["tgt"] % 8 == tau) & (syn["src"] % 8 != tau)])
         assert len(at15["ranks"][tau]["img_s"]) == len(used) < 1000 - 125
+        assert abs(len(used) - 875 * (1 - np.exp(-1))) < 5 * np.sqrt(875 * 0.25)
 
 
 def test_xi_off_is_the_flagged_layout():
