@@ -158,23 +158,53 @@ __global__ void image_fill(const uint64_t* dense, uint32_t N, uint32_t R, uint32
 
 // ---- all-sources images (threshold xi) ----
 // One (projection, target rank tau) pair: every source of the projection that lives
-// on another rank gets an image on tau.  Work item x of pair k is source x - first[k].
+// on another rank gets an image on tau.
 struct AllSrcPair {
   uint32_t src_first, n_src, src_stride, tau;
 };
+constexpr uint32_t kAllSrcChunk = 4096;   // sources per block of all_sources_flags
+
+// The x-th source of a pair.  Contiguous sources (stride 1) are visited rank by rank,
+// by local index within a rank -- x = off(k) + j for the gid src_first + k + j R, where
+// the first n_src mod R residues k hold one source more -- so consecutive threads mark
+// consecutive image rows; RemoteConnect sources (stride R) are in that order already.
+__device__ __forceinline__ uint32_t pair_source(const AllSrcPair& P, uint32_t R, uint32_t x) {
+  if (P.src_stride != 1) return P.src_first + x * P.src_stride;
+  const uint32_t q = P.n_src / R, rem = P.n_src - q * R, head = rem * (q + 1);
+  uint32_t k, j;
+  if (x < head) {
+    k = x / (q + 1);
+    j = x - k * (q + 1);
+  } else {                                  // q > 0 here: x < n_src = head + (R - rem) q
+    const uint32_t y = x - head;
+    k = rem + y / q;
+    j = y - (k - rem) * q;
+  }
+  return P.src_first + k + j * R;
+}
 
 // Marks the target-side image flag of dense row (slot of sigma, s) on tau (window
 // t0 .. t0 + nt - 1; tflag [nt][N]) and/or the source-side flag of S_{tau,sigma}
-// (sflag [sigma][tau][Mmax]).  Every write stores 1, so overlapping pairs need no atomics.
-__global__ void all_sources_flags(const AllSrcPair* pairs, const uint64_t* first /*[np + 1]*/, uint32_t np,
-                                  uint32_t R, uint64_t magic_R, uint32_t N, uint32_t t0,
+// (sflag [sigma][tau][Mmax]).  Block b takes chunk b - chunk_first[k] of pair k (at
+// most kAllSrcChunk sources).  Every write stores 1, so overlapping pairs need no atomics.
+__global__ void all_sources_flags(const AllSrcPair* pairs, const uint32_t* chunk_first /*[np + 1]*/,
+                                  uint32_t np, uint32_t R, uint64_t magic_R, uint32_t N, uint32_t t0,
                                   const uint32_t* dense_off, uint32_t* tflag, uint8_t* sflag, uint32_t Mmax) {
-  const uint64_t total = first[np];
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = upper_bound_u64(first, np + 1, x) - 1;
-    const AllSrcPair P = pairs[k];
-    const uint32_t gid = P.src_first + (uint32_t)(x - first[k]) * P.src_stride;
+  __shared__ uint32_t s_k;
+  if (threadIdx.x == 0) {
+    uint32_t lo = 0, hi = np;             // last k with chunk_first[k] <= blockIdx.x
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (chunk_first[mid] <= blockIdx.x) lo = mid; else hi = mid;
+    }
+    s_k = lo;
+  }
+  __syncthreads();
+  const AllSrcPair P = pairs[s_k];
+  const uint32_t x0 = (blockIdx.x - chunk_first[s_k]) * kAllSrcChunk;
+  const uint32_t x1 = min(P.n_src, x0 + kAllSrcChunk);
+  for (uint32_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+    const uint32_t gid = pair_source(P, R, x);
     const uint32_t s = (uint32_t)div_magic(gid, R, magic_R), sig = gid - s * R;
     if (sig == P.tau) continue;
     if (tflag) {
@@ -450,29 +480,31 @@ static int mark_all_sources(snn_ctx* c, const std::vector<DevProj>& projs, const
   const Geom& g = ctx_geom(c);
   const uint32_t R = g.R;
   std::vector<AllSrcPair> pairs;
-  std::vector<uint64_t> first(1, 0);
+  std::vector<uint32_t> chunk_first(1, 0);
   for (size_t p = 0; p < projs.size(); ++p) {
     const DevProj& P = projs[p];
+    if (P.n_src == 0) continue;
     for (uint32_t tau = t0; tau < t0 + nt; ++tau) {
       if (!all_src[p * R + tau]) continue;
+      const uint64_t nb = (uint64_t)chunk_first.back() + (P.n_src + kAllSrcChunk - 1) / kAllSrcChunk;
+      if (nb > 0x7FFFFFFFull) return ctx_fail(c, SNN_EINVAL, "maps: too many all-sources images");
       pairs.push_back({P.src_first, P.n_src, P.src_stride, tau});
-      first.push_back(first.back() + P.n_src);
+      chunk_first.push_back((uint32_t)nb);
     }
   }
-  if (pairs.empty() || first.back() == 0) return SNN_OK;
+  if (pairs.empty()) return SNN_OK;
   cudaStream_t st = ctx_stream(c);
   AllSrcPair* d_pairs = alloc_n<AllSrcPair>(c, pairs.size());
-  uint64_t* d_first = alloc_n<uint64_t>(c, first.size());
-  if (!d_pairs || !d_first) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
+  uint32_t* d_chunk = alloc_n<uint32_t>(c, chunk_first.size());
+  if (!d_pairs || !d_chunk) return ctx_fail(c, SNN_ENOMEM, "maps: allocation failed");
   MCK(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(AllSrcPair), cudaMemcpyHostToDevice, st));
-  MCK(cudaMemcpyAsync(d_first, first.data(), first.size() * 8, cudaMemcpyHostToDevice, st));
-  all_sources_flags<<<grid_for(c, first.back()), MB, 0, st>>>(d_pairs, d_first, (uint32_t)pairs.size(), R,
-                                                              g.magic_R, g.N, t0, ctx_dense_off(c), tflag, sflag,
-                                                              ctx_maps(c).Mmax);
+  MCK(cudaMemcpyAsync(d_chunk, chunk_first.data(), chunk_first.size() * 4, cudaMemcpyHostToDevice, st));
+  all_sources_flags<<<chunk_first.back(), MB, 0, st>>>(d_pairs, d_chunk, (uint32_t)pairs.size(), R, g.magic_R,
+                                                       g.N, t0, ctx_dense_off(c), tflag, sflag, ctx_maps(c).Mmax);
   MCK(cudaGetLastError());
   MCK(cudaStreamSynchronize(st));       // the host vectors above must outlive the copies
   ctx_free(c, d_pairs);
-  ctx_free(c, d_first);
+  ctx_free(c, d_chunk);
   return SNN_OK;
 }
 

@@ -3,8 +3,11 @@
     python -m paper_2512_09502_gb300.profile_cases update_500k       # update at 500k neurons
     python -m paper_2512_09502_gb300.profile_cases construction_112m # gen, sort, finalize
     python -m paper_2512_09502_gb300.profile_cases deliver_500k      # delivery, full-size ring
+    python -m paper_2512_09502_gb300.profile_cases images_xi_multi_area_r128
 
-Each builds one network and runs it; a profiler selects the kernel launches it wants.
+The first three build one network and run it; a profiler selects the kernel launches
+it wants.  The last measures the all-sources image threshold xi (0 and 1) on the
+multi-area network over 128 logical ranks and prints one JSON line per build.
 """
 from __future__ import annotations
 
@@ -52,7 +55,29 @@ def deliver_500k():
     print("spikes/step", s["n_spikes"] / 400, "events/step", s["n_events"] / 400)
 
 
-CASES = {"update_500k": update_500k, "construction_112m": construction_112m, "deliver_500k": deliver_500k}
+def images_xi_multi_area_r128():
+    """Flagged images (xi = 0) against all-sources images (xi = 1, the paper's value) on
+    the 32-area network over 128 ranks: map construction time, images, peak device
+    memory, and the simulation of 1,000 steps (images without connections add routed,
+    empty rows).  Each setting is built twice; the first build warms the allocator."""
+    import json
+    from . import workloads as wl
+    net = wl.multi_area(seed=1234, n_ranks=128)
+    for xi in (0.0, 1.0, 0.0, 1.0):
+        ctx = _ctx(net, xi=xi)
+        ctx.calibrate()
+        ctx.simulate(1000)
+        s = ctx.stats()
+        print(json.dumps({"xi": xi, "n_synapses": s["n_synapses"], "n_images": s["n_images"],
+                          "t_maps_ms": round(s["t_maps_ms"], 2), "t_calibrate_ms": round(s["t_calibrate_ms"], 2),
+                          "peak_device_GB": round(s["peak_device_bytes"] / 1e9, 3),
+                          "t_simulate_1000_steps_ms": round(s["t_simulate_ms"], 1),
+                          "spikes": s["n_spikes"], "events": s["n_events"]}), flush=True)
+        ctx.destroy()
+
+
+CASES = {"update_500k": update_500k, "construction_112m": construction_112m, "deliver_500k": deliver_500k,
+         "images_xi_multi_area_r128": images_xi_multi_area_r128}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
