@@ -124,6 +124,11 @@ struct snn_ctx {
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_steps = 0;
   bool capturing = false;
+  // overlapped steps (one rank): neuron work on st, delivery on st2, lists modulo 3
+  bool overlap = false;
+  SimArgs ov{};
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_u = nullptr, ev_d = nullptr;
   std::vector<uint32_t> host_gid_of;      // position -> gid
   std::vector<uint32_t> host_pos_of;      // gid -> position
 };
@@ -872,9 +877,24 @@ int snn_calibrate(snn_ctx* c) {
   }
   s.deliver_grid = (uint32_t)c->num_sms * (uint32_t)c->cfg.deliver_ctas_per_sm;
   s.update_grid = (uint32_t)c->num_sms * 8;
+  s.lists = 2;
   if (R > 1) {
     int rc = setup_routing(c);
     if (rc != SNN_OK) return rc;
+  } else {
+    // one rank: the neuron work of a step overlaps its delivery (two streams, lists
+    // modulo 3); a small neuron grid leaves the delivery most of every SM
+    c->ov = s;
+    c->ov.lists = 3;
+    c->ov.update_grid = (uint32_t)c->num_sms * 2;
+    AL(c->ov.n_work, 3, "overlapped spike counts");
+    AL(c->ov.work, (uint64_t)3 * N, "overlapped spike lists");
+    c->ov.work_stride = N;
+    CK(cudaMemsetAsync(c->ov.n_work, 0, 12, c->st));
+    if (!c->st2) CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    if (!c->ev_u) CK(cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming));
+    if (!c->ev_d) CK(cudaEventCreateWithFlags(&c->ev_d, cudaEventDisableTiming));
+    c->overlap = true;
   }
   CK(launch_init_state(s, d_v0, c->st));
   c->stats.kernel_launches += 1;
@@ -910,9 +930,39 @@ int snn_calibrate(snn_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------
+// Kernels one batch of `steps` steps launches.
+static uint64_t launches_per_batch(snn_ctx* c, uint32_t steps) {
+  if (c->overlap && !c->cfg.profile_kernels) return 2ull * steps + 2;
+  return (uint64_t)steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0)) + 1;
+}
+
+// One rank, overlapped: step_update(PRE) decides the spikes of the first step; then
+// per step k the delivery of step k (stream st2, after the neuron work that listed its
+// spikes) runs beside step_update(k) (stream st, after the delivery of step k - 1,
+// whose slots it reads).  The last step_update takes the input only.
+static int run_steps_overlapped(snn_ctx* c, uint32_t steps) {
+  SimArgs& o = c->ov;
+  cudaStream_t A = c->st, B = c->st2;
+  CK(launch_step_update(o, 0, kStepPre, A));
+  CK(cudaEventRecord(c->ev_u, A));
+  for (uint32_t k = 0; k < steps; ++k) {
+    if (k > 0) CK(cudaStreamWaitEvent(A, c->ev_d, 0));
+    CK(cudaStreamWaitEvent(B, c->ev_u, 0));
+    CK(launch_deliver(o, k, B, false));
+    CK(cudaEventRecord(c->ev_d, B));
+    CK(launch_step_update(o, k, kStepPost | (k + 1 < steps ? kStepPre : 0u), A));
+    CK(cudaEventRecord(c->ev_u, A));
+  }
+  CK(cudaStreamWaitEvent(A, c->ev_d, 0));
+  CK(launch_advance(o, steps, A));
+  if (!c->capturing) c->stats.kernel_launches += launches_per_batch(c, steps);
+  return SNN_OK;
+}
+
 static int run_steps(snn_ctx* c, uint32_t steps) {
   SimArgs& s = c->sim;
   if (steps == 0) return SNN_OK;
+  if (c->overlap && !c->cfg.profile_kernels) return run_steps_overlapped(c, steps);
   const bool routed = c->cfg.n_ranks > 1;
   const bool profile = c->cfg.profile_kernels && !c->capturing;
   std::vector<cudaEvent_t> evs;
@@ -920,12 +970,16 @@ static int run_steps(snn_ctx* c, uint32_t steps) {
     evs.resize(3 * (size_t)steps);
     for (auto& e : evs) CK(cudaEventCreate(&e));
   }
+  // programmatic dependent launches chain the kernels of a batch (not when each kernel
+  // is timed): every kernel but the batch's first update starts while its predecessor
+  // drains; the advance kernel after the batch is a normal launch
+  const bool pdl = !profile;
   for (uint32_t k = 0; k < steps; ++k) {
     if (profile) CK(cudaEventRecord(evs[3 * k], c->st));
-    CK(launch_update(s, k, c->st));
-    if (routed) CK(launch_route(c, k));
+    CK(launch_update(s, k, c->st, pdl && k > 0));
+    if (routed) CK(launch_route(c, k, pdl));
     if (profile) CK(cudaEventRecord(evs[3 * k + 1], c->st));
-    CK(launch_deliver(s, k, c->st));
+    CK(launch_deliver(s, k, c->st, pdl));
     if (profile) CK(cudaEventRecord(evs[3 * k + 2], c->st));
   }
   CK(launch_advance(s, steps, c->st));
@@ -942,7 +996,7 @@ static int run_steps(snn_ctx* c, uint32_t steps) {
     c->stats.update_launches += steps;
     c->stats.deliver_launches += steps;
   }
-  if (!c->capturing) c->stats.kernel_launches += (uint64_t)steps * (2 + (routed ? 1 : 0)) + 1;
+  if (!c->capturing) c->stats.kernel_launches += launches_per_batch(c, steps);
   return SNN_OK;
 }
 
@@ -986,7 +1040,7 @@ int snn_simulate(snn_ctx* c, uint32_t steps) {
     while (c->graph && left >= c->graph_steps) {
       CK(cudaGraphLaunch(c->graph, c->st));
       left -= c->graph_steps;
-      c->stats.kernel_launches += (uint64_t)c->graph_steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0)) + 1;
+      c->stats.kernel_launches += launches_per_batch(c, c->graph_steps);
     }
   }
   int rc = run_steps(c, left);
@@ -1191,6 +1245,9 @@ void snn_destroy(snn_ctx* c) {
   cudaSetDevice(c->cfg.device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->ev_u) cudaEventDestroy(c->ev_u);
+  if (c->ev_d) cudaEventDestroy(c->ev_d);
   std::vector<void*> ptrs;
   for (auto& kv : c->live) ptrs.push_back(kv.first);
   for (void* p : ptrs) dfree(c, p);

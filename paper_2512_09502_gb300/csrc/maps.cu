@@ -689,8 +689,10 @@ namespace {
 // One warp per spike: the warp reserves the spike's rows in the work list with one
 // atomic, then its lanes fill them in parallel, each row with the rank it belongs to.
 __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
-  const uint32_t n = *r.step + k_step;
-  const uint32_t nspk = r.n_spk[n & 1];
+  pdl_wait();                      // the update's spike list is complete
+  pdl_trigger();
+  const uint32_t n = __ldcg(r.step) + k_step;
+  const uint32_t nspk = __ldcg(r.n_spk + (n & 1));
   const uint32_t* spk = r.spk + (uint64_t)(n & 1) * r.N;
   if (blockIdx.x == 0 && threadIdx.x == 0) r.n_work[(n + 1) & 1] = 0;
   uint32_t* work = r.work + (uint64_t)(n & 1) * r.work_cap;
@@ -699,7 +701,7 @@ __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t k = gw; k < nspk; k += nw) {
-    const uint32_t i = spk[k];                               // neuron position
+    const uint32_t i = __ldcg(spk + k);                      // neuron position
     uint32_t lo = 0, hi = r.R;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
@@ -811,10 +813,10 @@ int setup_routing(snn_ctx* c) {
   return SNN_OK;
 }
 
-cudaError_t launch_route(snn_ctx* c, uint32_t k_step) {
+cudaError_t launch_route(snn_ctx* c, uint32_t k_step, bool pdl) {
   MapsState& m = ctx_maps(c);
-  route_kernel<<<(unsigned)std::max(1, ctx_num_sms(c) * 2), 256, 0, ctx_stream(c)>>>(m.route, k_step);
-  return cudaGetLastError();
+  return launch_pdl(route_kernel, dim3((unsigned)std::max(1, ctx_num_sms(c) * 2)), dim3(256), ctx_stream(c), pdl,
+                    m.route, k_step);
 }
 
 uint32_t route_kernels_per_step(snn_ctx* c) { return ctx_geom(c).R > 1 ? 1 : 0; }

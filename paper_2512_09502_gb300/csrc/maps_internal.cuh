@@ -70,7 +70,7 @@ int build_maps_dry(snn_ctx* c, uint32_t rank, const std::vector<DevProj>& projs,
 int build_maps(snn_ctx* c, const std::vector<DevProj>& projs, const DevProj* d_projs,
                const uint64_t* d_cbase, const uint32_t* d_tables, const std::vector<uint8_t>& all_src);
 int setup_routing(snn_ctx* c);
-cudaError_t launch_route(snn_ctx* c, uint32_t k_step);
+cudaError_t launch_route(snn_ctx* c, uint32_t k_step, bool pdl);
 uint32_t route_kernels_per_step(snn_ctx* c);
 int rank_row_ptr(snn_ctx* c, uint32_t rank, std::vector<uint64_t>* rp);
 int rank_row_scales(snn_ctx* c, uint32_t rank, std::vector<float>* scales);

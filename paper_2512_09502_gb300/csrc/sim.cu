@@ -43,54 +43,103 @@ __device__ __forceinline__ uint32_t table_count(const uint32_t* thr, uint32_t le
   return upper_bound_u32(thr, len, w);
 }
 
+// Poisson counts of the four neurons of one thread for drive dr at step n, from word
+// (g mod 4) of the block with counter (g div 4, n) (one block when the four are
+// consecutive gids on one rank); in[k]: neuron k is driven by dr.
+__device__ __forceinline__ void poisson_counts4(const SimArgs& a, const DevDrive& dr, const uint32_t* s_tbl,
+                                                uint32_t q, uint32_t n, bool full, const bool* live,
+                                                const uint32_t* gid, uint32_t* cnt, bool* in) {
+  uint32_t wd[UPD_Q];
+  if (a.R == 1 && full) {
+    const uint4 b = philox_stream((uint64_t)q | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
+    wd[0] = b.x; wd[1] = b.y; wd[2] = b.z; wd[3] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) {
+      wd[k] = 0u;
+      if (live[k]) {
+        const uint4 b = philox_stream((uint64_t)(gid[k] >> 2) | ((uint64_t)n << 32), dr.idx,
+                                      kPurposePoisson, dr.seed);
+        const uint32_t lo = (gid[k] & 1u) ? b.y : b.x, hi = (gid[k] & 1u) ? b.w : b.z;
+        wd[k] = (gid[k] & 2u) ? hi : lo;
+      }
+    }
+  }
+  uint32_t wmax = 0;
+#pragma unroll
+  for (int k = 0; k < UPD_Q; ++k) {
+    in[k] = live[k] && gid[k] - dr.first < dr.n;
+    cnt[k] = 0;
+    if (in[k]) wmax = wd[k] > wmax ? wd[k] : wmax;
+  }
+  const uint32_t* tb = s_tbl + dr.tbl_off;
+  if (dr.tbl_len <= 32) {          // one pass over the ascending thresholds serves all four
+    for (uint32_t j = 0; j < dr.tbl_len; ++j) {
+      const uint32_t t = tb[j];
+      if (t > wmax) break;
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) cnt[k] += t <= wd[k] ? 1u : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) cnt[k] = upper_bound_u32(tb, dr.tbl_len, wd[k]);
+  }
+}
+
 // One thread updates UPD_Q = 4 consecutive neuron positions: 16-byte loads and stores
 // of the state and ring slot (the host guarantees 16-byte aligned arrays and a ring
 // stride that is a multiple of 4) and, on one rank, a single Philox block for the four
 // Poisson counts (neuron g draws word g mod 4 of the block with counter (g div 4, n)).
+//
+// The spike decision of step n needs V, the currents and refractoriness of step n - 1
+// only: the ring input of step n enters the currents.  So everything up to the spike
+// append -- state loads, V propagation, the Poisson counts of up to EARLY_DRIVES drives,
+// the threshold, the V / refr stores and the append to list n & 1 -- precedes pdl_wait
+// and overlaps the previous step's delivery.  After the wait come the ring slot (read
+// and cleared), I <- P11 I + ring, the drives in drive order (the order of the method's
+// step), and the reset of list (n + 1) & 1, which the previous delivery reads.
+constexpr uint32_t EARLY_DRIVES = 2;
 __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_t k_step) {
   __shared__ uint32_t s_tbl[256];
   __shared__ DevPop s_pop[64];
   __shared__ DevDrive s_dr[MAX_SMEM_DRIVES];
   const int tid = threadIdx.x;
   const uint32_t lane = tid & 31;
-  const uint32_t n = *a.step + k_step;
+  const uint32_t n = __ldcg(a.step) + k_step;   // written only by the advance kernel
   for (uint32_t i = tid; i < a.poisson_tbl_len && i < 256; i += UPD_BLOCK) s_tbl[i] = a.poisson_tbl[i];
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
   for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
-  if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;   // next step's list
   const uint32_t slot = n & a.ring_mask;
   float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.ring_stride;
   float* rin = rex + a.ring_stride;
   const bool two = a.n_rec == 2;
+  const bool early = a.ndrives <= EARLY_DRIVES;
   const uint32_t nq = (a.N + UPD_Q - 1) / UPD_Q;
   bool staged = false;             // the shared tables are published by the first iteration's barrier
   for (uint32_t qb = blockIdx.x * UPD_BLOCK; qb < nq; qb += gridDim.x * UPD_BLOCK) {
     const uint32_t q = qb + tid;
     const uint32_t i0 = q * UPD_Q;
     const bool full = q < nq && i0 + UPD_Q <= a.N;
-    float V[UPD_Q], Iex[UPD_Q], Iin[UPD_Q], in_ex[UPD_Q], in_in[UPD_Q];
+    float V[UPD_Q], Iex[UPD_Q], Iin[UPD_Q];
     uint32_t refr[UPD_Q], pi[UPD_Q], gid[UPD_Q];
     bool live[UPD_Q], spike[UPD_Q];
-    // phase 1: every load of the four neurons (I_in is identically 0 with a merged ring)
+    // phase 1: the state loads of the four neurons (I_in is identically 0 with a merged ring)
     if (full) {
-      const float4 v = reinterpret_cast<const float4*>(a.V)[q];
-      const float4 e = reinterpret_cast<const float4*>(a.Iex)[q];
-      const float4 x = reinterpret_cast<const float4*>(rex)[q];
-      const uint2 r = reinterpret_cast<const uint2*>(a.refr)[q];
+      // state written by the previous update: L2 loads (no L1 line may outlive a step)
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(a.V) + q);
+      const float4 e = __ldcg(reinterpret_cast<const float4*>(a.Iex) + q);
+      const uint2 r = __ldcg(reinterpret_cast<const uint2*>(a.refr) + q);
       const uint2 p = reinterpret_cast<const uint2*>(a.pop_of)[q];
       V[0] = v.x; V[1] = v.y; V[2] = v.z; V[3] = v.w;
       Iex[0] = e.x; Iex[1] = e.y; Iex[2] = e.z; Iex[3] = e.w;
-      in_ex[0] = x.x; in_ex[1] = x.y; in_ex[2] = x.z; in_ex[3] = x.w;
       refr[0] = r.x & 0xFFFFu; refr[1] = r.x >> 16; refr[2] = r.y & 0xFFFFu; refr[3] = r.y >> 16;
       pi[0] = p.x & 0xFFFFu; pi[1] = p.x >> 16; pi[2] = p.y & 0xFFFFu; pi[3] = p.y >> 16;
       if (two) {
-        const float4 ii = reinterpret_cast<const float4*>(a.Iin)[q];
-        const float4 y = reinterpret_cast<const float4*>(rin)[q];
+        const float4 ii = __ldcg(reinterpret_cast<const float4*>(a.Iin) + q);
         Iin[0] = ii.x; Iin[1] = ii.y; Iin[2] = ii.z; Iin[3] = ii.w;
-        in_in[0] = y.x; in_in[1] = y.y; in_in[2] = y.z; in_in[3] = y.w;
       } else {
 #pragma unroll
-        for (int k = 0; k < UPD_Q; ++k) Iin[k] = in_in[k] = 0.f;
+        for (int k = 0; k < UPD_Q; ++k) Iin[k] = 0.f;
       }
 #pragma unroll
       for (int k = 0; k < UPD_Q; ++k) live[k] = true;
@@ -99,13 +148,12 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
       for (int k = 0; k < UPD_Q; ++k) {
         const uint32_t i = i0 + k;
         live[k] = q < nq && i < a.N;
-        V[k] = Iex[k] = Iin[k] = in_ex[k] = in_in[k] = 0.f;
+        V[k] = Iex[k] = Iin[k] = 0.f;
         refr[k] = pi[k] = 0;
         if (live[k]) {
-          V[k] = a.V[i]; Iex[k] = a.Iex[i];
-          refr[k] = a.refr[i]; pi[k] = a.pop_of[i];
-          in_ex[k] = rex[i];
-          if (two) { Iin[k] = a.Iin[i]; in_in[k] = rin[i]; }
+          V[k] = __ldcg(a.V + i); Iex[k] = __ldcg(a.Iex + i);
+          refr[k] = __ldcg(a.refr + i); pi[k] = a.pop_of[i];
+          if (two) Iin[k] = __ldcg(a.Iin + i);
         }
       }
     }
@@ -115,100 +163,40 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
       __syncthreads();
       staged = true;
     }
-    // phase 2: propagate state and synaptic input (independent chains)
-    float thr[UPD_Q], vre[UPD_Q];
-    uint32_t rst[UPD_Q];
-#pragma unroll
-    for (int k = 0; k < UPD_Q; ++k) {
-      thr[k] = 0.f; vre[k] = 0.f; rst[k] = 0;
-      if (live[k]) {
-        const DevPop P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
-        float v = V[k], ie = Iex[k], ii = Iin[k];
-        uint32_t rf = refr[k];
-        if (rf == 0) v = P.P22 * v + P.P21ex * ie + P.P21in * ii + P.P20 * P.Ie;
-        else --rf;
-        Iex[k] = P.P11ex * ie + in_ex[k];
-        Iin[k] = P.P11in * ii + in_in[k];
-        V[k] = v; refr[k] = rf;
-        thr[k] = P.Vth; vre[k] = P.Vreset; rst[k] = P.ref_steps;
-      }
-    }
-    // Poisson drives, in drive order; one pass over the ascending count thresholds
-    // serves all four neurons
-    for (uint32_t dq = 0; dq < a.ndrives; ++dq) {
-      const DevDrive dr = dq < MAX_SMEM_DRIVES ? s_dr[dq] : a.drives[dq];
-      uint32_t wd[UPD_Q], cnt[UPD_Q];
-      bool in[UPD_Q];
-      if (a.R == 1 && full) {
-        const uint4 b = philox_stream((uint64_t)q | ((uint64_t)n << 32), dr.idx, kPurposePoisson, dr.seed);
-        wd[0] = b.x; wd[1] = b.y; wd[2] = b.z; wd[3] = b.w;
-      } else {
-#pragma unroll
-        for (int k = 0; k < UPD_Q; ++k) {
-          wd[k] = 0u;
-          if (live[k]) {
-            const uint4 b = philox_stream((uint64_t)(gid[k] >> 2) | ((uint64_t)n << 32), dr.idx,
-                                          kPurposePoisson, dr.seed);
-            const uint32_t lo = (gid[k] & 1u) ? b.y : b.x, hi = (gid[k] & 1u) ? b.w : b.z;
-            wd[k] = (gid[k] & 2u) ? hi : lo;
-          }
-        }
-      }
-      uint32_t wmax = 0;
-#pragma unroll
-      for (int k = 0; k < UPD_Q; ++k) {
-        in[k] = live[k] && gid[k] - dr.first < dr.n;
-        cnt[k] = 0;
-        if (in[k]) wmax = wd[k] > wmax ? wd[k] : wmax;
-      }
-      const uint32_t* tb = s_tbl + dr.tbl_off;
-      if (dr.tbl_len <= 32) {
-        for (uint32_t j = 0; j < dr.tbl_len; ++j) {
-          const uint32_t t = tb[j];
-          if (t > wmax) break;
-#pragma unroll
-          for (int k = 0; k < UPD_Q; ++k) cnt[k] += t <= wd[k] ? 1u : 0u;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < UPD_Q; ++k) cnt[k] = upper_bound_u32(tb, dr.tbl_len, wd[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < UPD_Q; ++k) {
-        if (!in[k]) continue;
-        if (dr.weight >= 0.f || !two) Iex[k] += (float)cnt[k] * dr.weight;
-        else Iin[k] += (float)cnt[k] * dr.weight;
-      }
-    }
+    // phase 2: membrane potential (from the currents of step n - 1) and the spike decision
 #pragma unroll
     for (int k = 0; k < UPD_Q; ++k) {
       spike[k] = false;
-      if (live[k] && V[k] >= thr[k]) {
-        V[k] = vre[k];
-        refr[k] = rst[k];
-        spike[k] = true;
+      if (live[k]) {
+        const DevPop& P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
+        float v = V[k];
+        uint32_t rf = refr[k];
+        if (rf == 0) v = P.P22 * v + P.P21ex * Iex[k] + P.P21in * Iin[k] + P.P20 * P.Ie;
+        else --rf;
+        if (v >= P.Vth) {
+          v = P.Vreset;
+          rf = P.ref_steps;
+          spike[k] = true;
+        }
+        V[k] = v; refr[k] = rf;
       }
     }
-    // phase 3: stores, ring slot cleared, spikes appended
+    uint32_t cnt_e[EARLY_DRIVES][UPD_Q];
+    bool in_e[EARLY_DRIVES][UPD_Q];
+    if (early) {
+#pragma unroll
+      for (uint32_t dq = 0; dq < EARLY_DRIVES; ++dq)
+        if (dq < a.ndrives) poisson_counts4(a, s_dr[dq], s_tbl, q, n, full, live, gid, cnt_e[dq], in_e[dq]);
+    }
     if (full) {
       reinterpret_cast<float4*>(a.V)[q] = make_float4(V[0], V[1], V[2], V[3]);
-      reinterpret_cast<float4*>(a.Iex)[q] = make_float4(Iex[0], Iex[1], Iex[2], Iex[3]);
       reinterpret_cast<uint2*>(a.refr)[q] = make_uint2(refr[0] | (refr[1] << 16), refr[2] | (refr[3] << 16));
-      reinterpret_cast<float4*>(rex)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (two) {
-        reinterpret_cast<float4*>(a.Iin)[q] = make_float4(Iin[0], Iin[1], Iin[2], Iin[3]);
-        reinterpret_cast<float4*>(rin)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
     } else {
 #pragma unroll
       for (int k = 0; k < UPD_Q; ++k) {
         if (!live[k]) continue;
-        const uint32_t i = i0 + k;
-        a.V[i] = V[k];
-        a.Iex[i] = Iex[k];
-        a.refr[i] = (uint16_t)refr[k];
-        rex[i] = 0.f;
-        if (two) { a.Iin[i] = Iin[k]; rin[i] = 0.f; }
+        a.V[i0 + k] = V[k];
+        a.refr[i0 + k] = (uint16_t)refr[k];
       }
     }
 #pragma unroll
@@ -233,6 +221,254 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
             lb = __shfl_sync(mask, lb, leader);
             const unsigned long long ls = lb + off;
             if (ls < a.log_cap) a.log[ls] = make_uint2(n, gid[k]);
+          }
+        }
+      }
+    }
+    // phase 3: after the previous delivery -- synaptic input of step n, drives, ring cleared
+    pdl_wait();
+    if (qb == blockIdx.x * UPD_BLOCK) {
+      if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;   // next step's list
+      pdl_trigger();
+    }
+    float in_ex[UPD_Q], in_in[UPD_Q];
+    if (full) {
+      const float4 x = __ldcg(reinterpret_cast<const float4*>(rex) + q);
+      in_ex[0] = x.x; in_ex[1] = x.y; in_ex[2] = x.z; in_ex[3] = x.w;
+      if (two) {
+        const float4 y = __ldcg(reinterpret_cast<const float4*>(rin) + q);
+        in_in[0] = y.x; in_in[1] = y.y; in_in[2] = y.z; in_in[3] = y.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < UPD_Q; ++k) in_in[k] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        in_ex[k] = in_in[k] = 0.f;
+        if (live[k]) {
+          in_ex[k] = __ldcg(rex + i0 + k);
+          if (two) in_in[k] = __ldcg(rin + i0 + k);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) {
+      if (!live[k]) continue;
+      const DevPop& P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
+      Iex[k] = P.P11ex * Iex[k] + in_ex[k];
+      Iin[k] = P.P11in * Iin[k] + in_in[k];
+    }
+    for (uint32_t dq = 0; dq < a.ndrives; ++dq) {
+      const DevDrive dr = dq < MAX_SMEM_DRIVES ? s_dr[dq] : a.drives[dq];
+      uint32_t cnt[UPD_Q];
+      bool in[UPD_Q];
+      if (early) {
+#pragma unroll
+        for (int k = 0; k < UPD_Q; ++k) {
+          cnt[k] = dq == 0 ? cnt_e[0][k] : cnt_e[1][k];
+          in[k] = dq == 0 ? in_e[0][k] : in_e[1][k];
+        }
+      } else {
+        poisson_counts4(a, dr, s_tbl, q, n, full, live, gid, cnt, in);
+      }
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        if (!in[k]) continue;
+        if (dr.weight >= 0.f || !two) Iex[k] += (float)cnt[k] * dr.weight;
+        else Iin[k] += (float)cnt[k] * dr.weight;
+      }
+    }
+    if (full) {
+      reinterpret_cast<float4*>(a.Iex)[q] = make_float4(Iex[0], Iex[1], Iex[2], Iex[3]);
+      reinterpret_cast<float4*>(rex)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (two) {
+        reinterpret_cast<float4*>(a.Iin)[q] = make_float4(Iin[0], Iin[1], Iin[2], Iin[3]);
+        reinterpret_cast<float4*>(rin)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        if (!live[k]) continue;
+        a.Iex[i0 + k] = Iex[k];
+        rex[i0 + k] = 0.f;
+        if (two) { a.Iin[i0 + k] = Iin[k]; rin[i0 + k] = 0.f; }
+      }
+    }
+  }
+  if (blockIdx.x * UPD_BLOCK >= nq) {   // a CTA without neurons still keeps the protocol
+    pdl_wait();
+    if (blockIdx.x == 0 && tid == 0) a.n_spk[(n + 1) & 1] = 0;
+  }
+}
+
+// Neuron work of an overlapped step n (one rank): POST takes ring slot n (read and
+// cleared), I <- P11 I + ring, then the drives of step n in drive order; PRE decides the
+// spikes of step m (m = n + 1 after POST, m = n alone) from V, I and refractoriness of
+// step m - 1 and appends them to list m mod 3.  The delivery of step n runs meanwhile:
+// it reads list n mod 3 and adds into slots n + d, d >= 1, never into slot n.  The kernel
+// with POST resets list (n + 2) mod 3, which the delivery of step n - 1 (complete)
+// read and step_update(n + 1) fills.
+__global__ void __launch_bounds__(UPD_BLOCK, 4) step_update_kernel(SimArgs a, uint32_t k_step, uint32_t mode) {
+  __shared__ uint32_t s_tbl[256];
+  __shared__ DevPop s_pop[64];
+  __shared__ DevDrive s_dr[MAX_SMEM_DRIVES];
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31;
+  const uint32_t n = __ldcg(a.step) + k_step;
+  const bool post = mode & kStepPost, pre = mode & kStepPre;
+  const uint32_t m = post ? n + 1 : n;
+  const uint32_t lm = m % 3;
+  for (uint32_t i = tid; i < a.poisson_tbl_len && i < 256; i += UPD_BLOCK) s_tbl[i] = a.poisson_tbl[i];
+  for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
+  for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
+  if (post && blockIdx.x == 0 && tid == 0) a.n_work[(n + 2) % 3] = 0;
+  float* rex = a.ring + ((uint64_t)(n & a.ring_mask) * a.n_rec) * a.ring_stride;
+  float* rin = rex + a.ring_stride;
+  const bool two = a.n_rec == 2;
+  const uint32_t nq = (a.N + UPD_Q - 1) / UPD_Q;
+  bool staged = false;
+  for (uint32_t qb = blockIdx.x * UPD_BLOCK; qb < nq; qb += gridDim.x * UPD_BLOCK) {
+    const uint32_t q = qb + tid;
+    const uint32_t i0 = q * UPD_Q;
+    const bool full = q < nq && i0 + UPD_Q <= a.N;
+    float V[UPD_Q], Iex[UPD_Q], Iin[UPD_Q], in_ex[UPD_Q], in_in[UPD_Q];
+    uint32_t refr[UPD_Q], pi[UPD_Q], gid[UPD_Q];
+    bool live[UPD_Q], spike[UPD_Q];
+    if (full) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(a.V) + q);
+      const float4 e = __ldcg(reinterpret_cast<const float4*>(a.Iex) + q);
+      const uint2 r = __ldcg(reinterpret_cast<const uint2*>(a.refr) + q);
+      const uint2 p = reinterpret_cast<const uint2*>(a.pop_of)[q];
+      V[0] = v.x; V[1] = v.y; V[2] = v.z; V[3] = v.w;
+      Iex[0] = e.x; Iex[1] = e.y; Iex[2] = e.z; Iex[3] = e.w;
+      refr[0] = r.x & 0xFFFFu; refr[1] = r.x >> 16; refr[2] = r.y & 0xFFFFu; refr[3] = r.y >> 16;
+      pi[0] = p.x & 0xFFFFu; pi[1] = p.x >> 16; pi[2] = p.y & 0xFFFFu; pi[3] = p.y >> 16;
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) in_ex[k] = in_in[k] = Iin[k] = 0.f;
+      if (post) {
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(rex) + q);
+        in_ex[0] = x.x; in_ex[1] = x.y; in_ex[2] = x.z; in_ex[3] = x.w;
+      }
+      if (two) {
+        const float4 ii = __ldcg(reinterpret_cast<const float4*>(a.Iin) + q);
+        Iin[0] = ii.x; Iin[1] = ii.y; Iin[2] = ii.z; Iin[3] = ii.w;
+        if (post) {
+          const float4 y = __ldcg(reinterpret_cast<const float4*>(rin) + q);
+          in_in[0] = y.x; in_in[1] = y.y; in_in[2] = y.z; in_in[3] = y.w;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) live[k] = true;
+    } else {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        const uint32_t i = i0 + k;
+        live[k] = q < nq && i < a.N;
+        V[k] = Iex[k] = Iin[k] = in_ex[k] = in_in[k] = 0.f;
+        refr[k] = pi[k] = 0;
+        if (live[k]) {
+          V[k] = __ldcg(a.V + i); Iex[k] = __ldcg(a.Iex + i);
+          refr[k] = __ldcg(a.refr + i); pi[k] = a.pop_of[i];
+          if (post) in_ex[k] = __ldcg(rex + i);
+          if (two) {
+            Iin[k] = __ldcg(a.Iin + i);
+            if (post) in_in[k] = __ldcg(rin + i);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) gid[k] = live[k] ? i0 + k : 0u;   // one rank: position = gid
+    if (!staged) {
+      __syncthreads();
+      staged = true;
+    }
+    if (post) {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        if (!live[k]) continue;
+        const DevPop& P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
+        Iex[k] = P.P11ex * Iex[k] + in_ex[k];
+        Iin[k] = P.P11in * Iin[k] + in_in[k];
+      }
+      for (uint32_t dq = 0; dq < a.ndrives; ++dq) {
+        const DevDrive dr = dq < MAX_SMEM_DRIVES ? s_dr[dq] : a.drives[dq];
+        uint32_t cnt[UPD_Q];
+        bool in[UPD_Q];
+        poisson_counts4(a, dr, s_tbl, q, n, full, live, gid, cnt, in);
+#pragma unroll
+        for (int k = 0; k < UPD_Q; ++k) {
+          if (!in[k]) continue;
+          if (dr.weight >= 0.f || !two) Iex[k] += (float)cnt[k] * dr.weight;
+          else Iin[k] += (float)cnt[k] * dr.weight;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) {
+      spike[k] = false;
+      if (pre && live[k]) {
+        const DevPop& P = pi[k] < 64 ? s_pop[pi[k]] : a.pops[pi[k]];
+        float v = V[k];
+        uint32_t rf = refr[k];
+        if (rf == 0) v = P.P22 * v + P.P21ex * Iex[k] + P.P21in * Iin[k] + P.P20 * P.Ie;
+        else --rf;
+        if (v >= P.Vth) {
+          v = P.Vreset;
+          rf = P.ref_steps;
+          spike[k] = true;
+        }
+        V[k] = v; refr[k] = rf;
+      }
+    }
+    if (full) {
+      if (pre) {
+        reinterpret_cast<float4*>(a.V)[q] = make_float4(V[0], V[1], V[2], V[3]);
+        reinterpret_cast<uint2*>(a.refr)[q] = make_uint2(refr[0] | (refr[1] << 16), refr[2] | (refr[3] << 16));
+      }
+      if (post) {
+        reinterpret_cast<float4*>(a.Iex)[q] = make_float4(Iex[0], Iex[1], Iex[2], Iex[3]);
+        reinterpret_cast<float4*>(rex)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (two) {
+          reinterpret_cast<float4*>(a.Iin)[q] = make_float4(Iin[0], Iin[1], Iin[2], Iin[3]);
+          reinterpret_cast<float4*>(rin)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < UPD_Q; ++k) {
+        if (!live[k]) continue;
+        const uint32_t i = i0 + k;
+        if (pre) { a.V[i] = V[k]; a.refr[i] = (uint16_t)refr[k]; }
+        if (post) {
+          a.Iex[i] = Iex[k];
+          rex[i] = 0.f;
+          if (two) { a.Iin[i] = Iin[k]; rin[i] = 0.f; }
+        }
+      }
+    }
+    if (!pre) continue;
+#pragma unroll
+    for (int k = 0; k < UPD_Q; ++k) {
+      const uint32_t mask = __ballot_sync(0xffffffffu, spike[k]);
+      if (mask) {
+        const int leader = __ffs(mask) - 1;
+        uint32_t sbase = 0;
+        if ((int)lane == leader) {
+          sbase = atomicAdd(&a.n_work[lm], __popc(mask));
+          atomicAdd(a.n_spikes_total, (unsigned long long)__popc(mask));
+        }
+        sbase = __shfl_sync(0xffffffffu, sbase, leader);
+        const uint32_t off = __popc(mask & ((1u << lane) - 1));
+        if (spike[k]) {
+          a.work[(uint64_t)lm * a.work_stride + sbase + off] = i0 + k;
+          if (a.log_cap) {
+            unsigned long long lb = 0;
+            if ((int)lane == leader) lb = atomicAdd(a.n_logged, (unsigned long long)__popc(mask));
+            lb = __shfl_sync(mask, lb, leader);
+            const unsigned long long ls = lb + off;
+            if (ls < a.log_cap) a.log[ls] = make_uint2(m, gid[k]);
           }
         }
       }
@@ -329,21 +565,24 @@ __device__ __forceinline__ void add_events(const SimArgs& a, unsigned long long 
 template <typename WT>
 __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT* __restrict__ w,
                                                             uint32_t k_step) {
-  const uint32_t n = *a.step + k_step;
-  const uint32_t nitems = a.n_work[n & 1];
-  const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
-  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)(n & 1) * a.work_stride : nullptr;
+  pdl_wait();                      // the step's list is complete
+  pdl_trigger();
+  const uint32_t n = __ldcg(a.step) + k_step;
+  const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
+  const uint32_t nitems = __ldcg(a.n_work + li);
+  const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
+  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)li * a.work_stride : nullptr;
   const uint32_t slices = a.slices;
   const uint64_t total = (uint64_t)nitems * slices;
   const uint64_t pol_stream = policy_evict_first(), pol_ring = policy_evict_last();
   for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
     const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
-    const uint32_t row = items[si];
+    const uint32_t row = __ldcg(items + si);
     const uint64_t ra = a.rows[row], rb = a.rows[row + 1];
     const uint64_t len = rb - ra;
     const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
     const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
-    const uint32_t toff = taus ? a.rank_off[taus[si]] : 0u;   // first neuron position of the row's rank
+    const uint32_t toff = taus ? a.rank_off[__ldcg(taus + si)] : 0u;   // first neuron position of the row's rank
     deliver_span<WT, DEL_BLOCK>(a, w, n, lo, hi, threadIdx.x, DEL_BLOCK, toff, sc, pol_stream, pol_ring);
     if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);   // a few per CTA
   }
@@ -354,10 +593,13 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
 template <typename WT>
 __global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, const WT* __restrict__ w,
                                                                  uint32_t k_step) {
-  const uint32_t n = *a.step + k_step;
-  const uint32_t nitems = a.n_work[n & 1];
-  const uint32_t* items = a.work + (uint64_t)(n & 1) * a.work_stride;
-  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)(n & 1) * a.work_stride : nullptr;
+  pdl_wait();                      // the step's list is complete
+  pdl_trigger();
+  const uint32_t n = __ldcg(a.step) + k_step;
+  const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
+  const uint32_t nitems = __ldcg(a.n_work + li);
+  const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
+  const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)li * a.work_stride : nullptr;
   const uint32_t L = a.item_lanes;                     // 4, 8, 16 or 32
   const uint32_t lane = threadIdx.x & 31, sub = lane / L, sl = lane % L, per_warp = 32 / L;
   const uint64_t gw = ((uint64_t)blockIdx.x * DEL_BLOCK + threadIdx.x) >> 5;
@@ -370,10 +612,10 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, cons
     uint32_t toff = 0;
     float sc = 1.0f;
     if (it < nitems) {
-      const uint32_t row = items[it];
+      const uint32_t row = __ldcg(items + it);
       lo = a.rows[row];
       hi = a.rows[row + 1];
-      toff = taus ? a.rank_off[taus[it]] : 0u;
+      toff = taus ? a.rank_off[__ldcg(taus + it)] : 0u;
       if (a.row_scale) sc = a.row_scale[row];
       if (sl == 0) events += hi - lo;
     }
@@ -395,24 +637,29 @@ __global__ void init_state_kernel(SimArgs a, const float* v0) {
   }
 }
 
-cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
+cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st, bool pdl) {
   const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_Q - 1) / (UPD_BLOCK * UPD_Q);
   const unsigned grid = (unsigned)(need < a.update_grid ? need : a.update_grid);
-  update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a, k_step);
-  return cudaGetLastError();
+  return launch_pdl(update_kernel, dim3(grid), dim3(UPD_BLOCK), st, pdl, a, k_step);
 }
 
 template <typename WT>
-static void launch_deliver_t(const SimArgs& a, const WT* w, uint32_t k_step, cudaStream_t st) {
-  const unsigned grid = (unsigned)a.deliver_grid;
-  if (a.item_lanes) deliver_rows_kernel<WT><<<grid, DEL_BLOCK, 0, st>>>(a, w, k_step);
-  else deliver_kernel<WT><<<grid, DEL_BLOCK, 0, st>>>(a, w, k_step);
+static cudaError_t launch_deliver_t(const SimArgs& a, const WT* w, uint32_t k_step, cudaStream_t st, bool pdl) {
+  const dim3 grid((unsigned)a.deliver_grid);
+  if (a.item_lanes) return launch_pdl(deliver_rows_kernel<WT>, grid, dim3(DEL_BLOCK), st, pdl, a, w, k_step);
+  return launch_pdl(deliver_kernel<WT>, grid, dim3(DEL_BLOCK), st, pdl, a, w, k_step);
 }
 
-cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st) {
-  if (a.w_format == 0) launch_deliver_t(a, (const float*)a.w, k_step, st);
-  else if (a.w_format == 1) launch_deliver_t(a, (const __nv_bfloat16*)a.w, k_step, st);
-  else launch_deliver_t(a, (const __half*)a.w, k_step, st);
+cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st, bool pdl) {
+  if (a.w_format == 0) return launch_deliver_t(a, (const float*)a.w, k_step, st, pdl);
+  if (a.w_format == 1) return launch_deliver_t(a, (const __nv_bfloat16*)a.w, k_step, st, pdl);
+  return launch_deliver_t(a, (const __half*)a.w, k_step, st, pdl);
+}
+
+cudaError_t launch_step_update(const SimArgs& a, uint32_t k_step, uint32_t mode, cudaStream_t st) {
+  const uint64_t need = ((uint64_t)a.N + UPD_BLOCK * UPD_Q - 1) / (UPD_BLOCK * UPD_Q);
+  const unsigned grid = (unsigned)(need < a.update_grid ? need : a.update_grid);
+  step_update_kernel<<<grid, UPD_BLOCK, 0, st>>>(a, k_step, mode);
   return cudaGetLastError();
 }
 

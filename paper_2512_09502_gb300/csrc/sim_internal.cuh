@@ -30,10 +30,45 @@ struct SimArgs {
   const float* row_scale;                     // per row (fp16 format) or null
   uint32_t slices;                            // slices of one row (several CTAs per row)
   uint32_t deliver_grid, update_grid;
+  uint32_t lists;                             // spike / work lists cycled: 2, or 3 (overlapped steps)
 };
 
-cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st);
-cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st);
+// Overlapped steps (one rank): the neuron work of step k and the delivery of step k run
+// as two concurrent kernels.  step_update(k) takes the synaptic input of step k (POST)
+// and decides the spikes of step k + 1 (PRE); a batch starts with PRE alone for its first
+// step and ends with POST alone.  Lists cycle modulo 3.
+constexpr uint32_t kStepPost = 1, kStepPre = 2;
+cudaError_t launch_step_update(const SimArgs& a, uint32_t k_step, uint32_t mode, cudaStream_t st);
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic stream serialization attribute may start while the previous kernel of the
+// stream still runs.  pdl_wait blocks until that kernel has completed and its writes are
+// visible; under a normal launch it returns at once.  pdl_trigger lets the next kernel's
+// CTAs be scheduled before this one ends.  Only work that touches nothing the previous
+// kernel writes may precede pdl_wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches kern<<<grid, block, 0, st>>>(args...), with programmatic serialization when pdl.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// pdl: start while the previous kernel of the stream runs (every kernel of a step
+// but the first update of a batch)
+cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st, bool pdl);
+cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st, bool pdl);
 cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st);
 cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st);
 

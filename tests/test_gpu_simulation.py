@@ -87,6 +87,40 @@ def test_graph_and_stream_paths_agree():
         assert s["n_events"] == int(np.sum(rp[g.astype(np.int64) + 1] - rp[g.astype(np.int64)]))
 
 
+def test_overlapped_steps_match_the_sequential_schedule():
+    """One rank runs the neuron work of step k beside the delivery of step k (two
+    streams, spikes of step k + 1 decided one step ahead).  Against the sequential
+    update -> deliver chain (profile_kernels): the same early spikes, and after
+    simulate(T) nothing of step T is visible -- no logged spike at step >= T, the same
+    state within rounding as the sequential run after T steps."""
+    p = wl.NeuronParams(V_init_lo=0.0, V_init_hi=19.9, v_init_seed=5)
+    net = wl.balanced(1001, 250, 37, 9, wl.DELAY_NORMAL, seed=3, params=p, drive_rate_hz=20000.0)
+    seq = gpu_build(net, spike_log_capacity=1 << 20, use_graph=False, profile_kernels=True)
+    ovl = gpu_build(net, spike_log_capacity=1 << 20, use_graph=False)
+    for T in (1, 2, 5, 12, 20):      # 40 steps in calls of several lengths
+        seq.simulate(T)
+        ovl.simulate(T)
+        ss, gs = seq.get_spikes()
+        so, go = ovl.get_spikes()
+        assert so.astype(np.int64).max(initial=-1) < seq.stats()["steps_done"]
+        np.testing.assert_array_equal(ss, so)
+        np.testing.assert_array_equal(gs, go)
+        # ring sums are float atomics in free order: state within rounding
+        Vs, Es, Is = seq.get_state(0, net.n_neurons)
+        Vo, Eo, Io = ovl.get_state(0, net.n_neurons)
+        assert np.max(np.abs(Vs - Vo)) <= 1e-4
+        assert np.max(np.abs(Es - Eo)) <= 1e-5 * max(1.0, float(np.max(np.abs(Es))))
+        assert np.max(np.abs(Is - Io)) <= 1e-5 * max(1.0, float(np.max(np.abs(Is))))
+    assert seq.stats()["n_spikes"] == ovl.stats()["n_spikes"] > 50
+    g = gpu_build(net, spike_log_capacity=1 << 20, use_graph=True)
+    g.simulate(40)
+    sg, gg = g.get_spikes()
+    ss, gs = seq.get_spikes()
+    np.testing.assert_array_equal(sg, ss)
+    np.testing.assert_array_equal(gg, gs)
+    assert sg.max() < 40
+
+
 def _rates(net, steps, stored_fp32):
     ctx = gpu_build(net, spike_log_capacity=1 << 24)
     ctx.simulate(steps)
