@@ -100,7 +100,8 @@ typedef struct snn_config {
   int32_t exchange;            /* SNN_EXCHANGE_* (used when n_ranks > 1)               */
   int32_t use_graph;           /* capture the simulation step as a CUDA graph          */
   uint64_t spike_log_capacity; /* spikes kept for snn_get_spikes; 0 = no recording    */
-  int32_t radix_bits;          /* widest sort digit: 8 or 9 (mixed 8/9-bit plan); 0 = 9 */
+  int32_t radix_bits;          /* widest sort digit: 8, 9 or 10 (8-bit digits widened
+                                  as the key needs); 0 = 10                             */
   int32_t device;              /* CUDA device ordinal                                  */
   int32_t profile_kernels;     /* time every update / deliver launch with CUDA events
                                   (no graph then); results in snn_stats_t              */

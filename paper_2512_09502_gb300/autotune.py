@@ -18,7 +18,7 @@ from . import _lib
 
 CACHE = os.environ.get("SNN_AUTOTUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
-SORT_SPACE = [(rb, it) for rb in (8, 9) for it in (8, 12, 16)]
+SORT_SPACE = [(rb, it) for rb in (8, 9, 10) for it in (8, 12, 16)]
 DELIVER_SPACE = (4, 8, 16)
 
 

@@ -349,7 +349,7 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
   if (cudaSetDevice(config->device) != cudaSuccess) return SNN_ECUDA;
   snn_ctx* c = new snn_ctx();
   c->cfg = *config;
-  if (c->cfg.radix_bits == 0) c->cfg.radix_bits = 9;
+  if (c->cfg.radix_bits == 0) c->cfg.radix_bits = 10;
   if (c->cfg.sort_items == 0) c->cfg.sort_items = 16;
   if (c->cfg.deliver_ctas_per_sm == 0) c->cfg.deliver_ctas_per_sm = 8;
   if (alloc) c->alloc = *alloc;
@@ -520,29 +520,33 @@ int snn_calibrate(snn_ctx* c) {
   g.R = R; g.N = N;
   g.rb = R > 1 ? bits_for(R - 1) : 0;
   g.sb = bits_for(maxM - 1);
-  g.db = bits_for(dmax);
-  g.key_bits = g.rb + g.sb + g.db;
+  g.key_bits = g.rb + g.sb;
   g.cbits = std::max(1u, bits_for(ctot ? ctot - 1 : 0));
   g.magic_R = magic_for(R);
   if (g.key_bits + g.cbits > 64 && !c->cfg.dry_run)
     return fail(c, SNN_EINVAL, "network too large for 64-bit sort records");
-  // pass plan: as few passes as digits of at most radix_bits allow, 8-bit digits
-  // wherever possible (a 9-bit pass costs more than an 8-bit one)
+  // pass plan: as few passes as digits of at most radix_bits allow; digits are 8 bits
+  // wherever possible and widen one bit at a time (9, then 10) as the key requires, the
+  // widest ones last (a wider pass costs more than an 8-bit one)
   const uint32_t RB = (uint32_t)c->cfg.radix_bits;
   const uint32_t BINS = kHistStride;
-  const uint32_t passes = (g.key_bits + RB - 1) / RB;
+  const uint32_t passes = std::max(1u, (g.key_bits + RB - 1) / RB);
   if (passes > 6) return fail(c, SNN_EINVAL, "sort key too wide");
   uint8_t pass_bits[8] = {0}, pass_shift[8] = {0};
   {
-    const int nine = std::max(0, (int)g.key_bits - 8 * (int)passes);
+    uint32_t w[8];
+    for (uint32_t p = 0; p < passes; ++p) w[p] = 8;
+    int extra = (int)g.key_bits - 8 * (int)passes;        // bits beyond 8 per digit
+    for (uint32_t round = 0; round < 2 && extra > 0; ++round)
+      for (int p = (int)passes - 1; p >= 0 && extra > 0; --p)
+        if (w[p] < RB) { ++w[p]; --extra; }
     uint32_t left = g.key_bits, sh = 0;
     for (uint32_t p = 0; p < passes; ++p) {
-      uint32_t w = (p >= passes - (uint32_t)nine) ? 9u : 8u;
-      w = std::min(w, left);
-      pass_bits[p] = (uint8_t)w;
+      const uint32_t b = std::min(w[p], left);
+      pass_bits[p] = (uint8_t)b;
       pass_shift[p] = (uint8_t)sh;
-      sh += w;
-      left -= w;
+      sh += b;
+      left -= b;
     }
   }
 
@@ -551,6 +555,16 @@ int snn_calibrate(snn_ctx* c) {
   UP(d_projs, dp, "projections");
   uint32_t* d_dtab;
   UP(d_dtab, dtab, "delay and gap tables");
+  // delay guide tables for the finalize step: cell k counts the thresholds <= k << 24
+  std::vector<uint8_t> dguide((size_t)P * kDelayGuideCells, 0);
+  for (uint32_t i = 0; i < P; ++i) {
+    const ProjSpec& s = c->projs[i];
+    for (uint32_t k = 0; k < kDelayGuideCells; ++k)
+      dguide[(size_t)i * kDelayGuideCells + k] =
+          (uint8_t)(std::upper_bound(s.d_thr.begin(), s.d_thr.end(), k << 24) - s.d_thr.begin());
+  }
+  uint8_t* d_dguide;
+  UP(d_dguide, dguide, "delay guide tables");
   std::vector<uint32_t> ft_proj, pb_proj;
   std::vector<uint64_t> ft_tile_first(1, 0), pb_t_first(1, 0);
   for (uint32_t i = 0; i < P; ++i) {
@@ -703,7 +717,7 @@ int snn_calibrate(snn_ctx* c) {
 
   a.blocks = d_blocks; a.nblocks = (uint32_t)blocks.size();
   a.n_gen_tiles = tiles;
-  a.projs = d_projs; a.nproj = P; a.dtables = d_dtab; a.g = g;
+  a.projs = d_projs; a.nproj = P; a.dtables = d_dtab; a.dguide = d_dguide; a.g = g;
   a.rec_a = rec_a; a.rec_b = rec_b; a.hist = hist; a.bin_base = bin_base;
   a.seg_start = c->d_seg_start; a.seg_tile0 = d_seg_tile0; a.status = status;
   a.counters = counters; a.err = c->d_err; a.passes = passes; a.radix_bits = RB;
@@ -771,6 +785,7 @@ int snn_calibrate(snn_ctx* c) {
   CK(cudaEventRecord(ev[3], c->st));
   dfree(c, cur);
   dfree(c, d_blocks);
+  dfree(c, d_dguide);
   dfree(c, counters);
   for (void* p : counted_bufs) dfree(c, p);
 

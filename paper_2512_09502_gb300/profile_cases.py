@@ -36,7 +36,7 @@ def construction_112m():
     """100k neurons, in-degree 900 + 225: 112.5M synapses (about 1.9 GB at peak)."""
     from . import workloads as wl
     net = wl.balanced(80000, 20000, 900, 225, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0)
-    ctx = _ctx(net, radix_bits=9, sort_items=16, deliver_ctas_per_sm=16)
+    ctx = _ctx(net, radix_bits=10, sort_items=16, deliver_ctas_per_sm=16)
     ctx.calibrate()
     s = ctx.stats()
     print("synapses", s["n_synapses"], "gen", s["t_generate_ms"], "sort", s["t_sort_ms"], "finalize",
@@ -48,7 +48,7 @@ def deliver_500k():
     5.625G-synapse workload): the full-size 128 MB ring with a 450M-synapse layout."""
     from . import workloads as wl
     net = wl.balanced(400000, 100000, 720, 180, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0, j_scale=12.5)
-    ctx = _ctx(net, use_graph=False, radix_bits=9, sort_items=16, deliver_ctas_per_sm=16)
+    ctx = _ctx(net, use_graph=False, radix_bits=10, sort_items=16, deliver_ctas_per_sm=16)
     ctx.calibrate()
     ctx.simulate(400)
     s = ctx.stats()

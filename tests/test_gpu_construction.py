@@ -29,6 +29,25 @@ def test_balanced_5k_bit_exact():
     _check(wl.balanced_small())
 
 
+@pytest.mark.parametrize("rb", [8, 9, 10])
+@pytest.mark.parametrize("items", [8, 12, 16])
+@pytest.mark.parametrize("R", [1, 3])
+def test_every_sort_kernel_width(rb, items, R):
+    """Every digit width and tile (8, 12, 16 records per thread) of the radix sort on a
+    19-bit key -- 300,001 neurons with K = 2 + 1: 19 source bits on one rank, 2 slot bits
+    + 17 on three -- sorted in digits of 8, 8, 3 bits (widest digit 8 or 9) or 9, 10 bits
+    (widest 10), over ~110 tiles with a ragged tail, bit-exact against the oracle."""
+    net = wl.balanced(240001, 60000, 2, 1, wl.DELAY_NORMAL, seed=rb * 100 + items, n_ranks=R)
+    ctx = gpu_build(net, radix_bits=rb, sort_items=items)
+    syn, ref = oracle_layout(net)
+    for tau in range(R):
+        compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
+    st = ctx.stats()
+    assert st["n_synapses"] == len(syn["src"]) and st["radix_bits"] == rb
+    assert st["key_bits"] == 19 and st["sort_passes"] == (2 if rb == 10 else 3)
+    ctx.destroy()
+
+
 @pytest.mark.parametrize("ne,ni,ke,ki", [(300, 75, 40, 10), (1001, 250, 37, 9), (4097, 3, 5, 1), (17, 2, 1, 1)])
 def test_ragged_sizes_normal_delays(ne, ni, ke, ki):
     _check(wl.balanced(ne, ni, ke, ki, wl.DELAY_NORMAL, seed=ne))
