@@ -243,6 +243,61 @@ __device__ __forceinline__ uint64_t look_back(const BuildArgs& a, uint64_t tile,
   }
 }
 
+// Two adjacent status words (bins b and b + 1, b even: one 16-byte access)
+__device__ __forceinline__ ulonglong2 ld_status2(const uint64_t* p) {
+  ulonglong2 v;
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_status2(uint64_t* p, uint64_t v0, uint64_t v1) {
+  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" :: "l"(p), "l"(v0), "l"(v1) : "memory");
+}
+__device__ __forceinline__ bool status_ready(uint64_t s, uint32_t epoch) {
+  return (s >> 62) != 0 && ((s >> 46) & 0xFFFF) == (epoch & 0xFFFF);
+}
+
+// look_back for the bins b0 and b0 + 1 of one thread (10-bit digits: two bins per
+// thread) in one walk: each predecessor's pair of status words is one 16-byte load, and
+// the walk ends when both bins have met an inclusive prefix.  The same bounded wait.
+__device__ __forceinline__ void look_back2(const BuildArgs& a, uint64_t tile, uint64_t first_tile, uint32_t b0,
+                                           uint32_t bins, uint32_t epoch, uint64_t& ex0, uint64_t& ex1) {
+  constexpr int W = 4;
+  ex0 = 0;
+  ex1 = 0;
+  bool done0 = false, done1 = false;
+  uint64_t k = tile - 1;                    // tile > first_tile here
+  while (true) {
+    ulonglong2 st[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      st[w] = (k >= first_tile + w) ? ld_status2(a.status + (k - w) * bins + b0) : make_ulonglong2(0, 0);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      ulonglong2 s = st[w];
+      const uint64_t* sp = a.status + (k - w) * bins + b0;
+      uint32_t spins = 0;
+      while ((!done0 && !status_ready(s.x, epoch)) || (!done1 && !status_ready(s.y, epoch))) {
+        if (++spins > SPIN_LIMIT || (*(volatile uint32_t*)a.err & kErrTimeout)) {
+          atomicOr(a.err, kErrTimeout);
+          return;
+        }
+        __nanosleep(32);
+        s = ld_status2(sp);
+      }
+      if (!done0) {
+        ex0 += s.x & ST_VAL;
+        done0 = (s.x >> 62) == 2;
+      }
+      if (!done1) {
+        ex1 += s.y & ST_VAL;
+        done1 = (s.y >> 62) == 2;
+      }
+      if (done0 && done1) return;           // the segment's first tile is always inclusive
+    }
+    k -= W;
+  }
+}
+
 // Self-test of the bounded wait: tile 1 looks back at tile 0, whose status is never
 // published, so every bin's wait must give up and flag kErrTimeout.
 __global__ void bounded_wait_selftest(BuildArgs a, uint32_t bins) {
@@ -265,6 +320,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
   constexpr int BINS = 1 << RB;
   constexpr int NW = SORT_BLOCK / 32;
   constexpr int BPT = (BINS + SORT_BLOCK - 1) / SORT_BLOCK;   // bins per thread
+  static_assert(BPT == 1 || BINS == 2 * SORT_BLOCK, "two bins per thread only for 10-bit digits");
   constexpr int TILE = SORT_BLOCK * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem<RB, ITEMS>& sm = *reinterpret_cast<SortSmem<RB, ITEMS>*>(smem_raw);
@@ -348,10 +404,14 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
   const bool first = tile == first_tile;
   const uint64_t ep = (uint64_t)(epoch & 0xFFFF) << 46;
   uint64_t* strow = a.status + tile * BINS;
+  if constexpr (BPT == 2) {
+    st_status2(strow + tid * 2, (first ? ST_INC : ST_AGG) | ep | tot[0], (first ? ST_INC : ST_AGG) | ep | tot[1]);
+  } else {
 #pragma unroll
-  for (int q = 0; q < BPT; ++q) {
-    const int b = tid * BPT + q;
-    if (b < BINS) st_status(strow + b, (first ? ST_INC : ST_AGG) | ep | tot[q]);
+    for (int q = 0; q < BPT; ++q) {
+      const int b = tid * BPT + q;
+      if (b < BINS) st_status(strow + b, (first ? ST_INC : ST_AGG) | ep | tot[q]);
+    }
   }
 
   // tile-local exclusive scan of the bin counts (thread-contiguous bins)
@@ -386,17 +446,29 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
       sm.stage[sm.binstart[d] + sm.whist[warp][d] + rnk[j]] = rec[j];
     }
   }
-#pragma unroll
-  for (int q = 0; q < BPT; ++q) {
-    const int b = tid * BPT + q;
-    if (b >= BINS) continue;
-    uint64_t excl = 0;
+  const uint64_t* bbase = a.bin_base + ((uint64_t)seg * a.passes + pass) * kHistStride;
+  if constexpr (BPT == 2) {        // 10-bit digits: bins 2 tid and 2 tid + 1, one walk
+    const uint32_t b0 = (uint32_t)tid * 2;
+    uint64_t e0 = 0, e1 = 0;
     if (!first) {
-      excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
-      st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
+      look_back2(a, tile, first_tile, b0, BINS, epoch, e0, e1);
+      st_status2(strow + b0, ST_INC | ep | ((e0 + tot[0]) & ST_VAL), ST_INC | ep | ((e1 + tot[1]) & ST_VAL));
     }
-    // global position of staged element k of bin b = gbase[b] + k
-    sm.gbase[b] = a.bin_base[((uint64_t)seg * a.passes + pass) * kHistStride + b] + excl - bstart[q];
+    sm.gbase[b0] = bbase[b0] + e0 - bstart[0];
+    sm.gbase[b0 + 1] = bbase[b0 + 1] + e1 - bstart[1];
+  } else {
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+      const int b = tid * BPT + q;
+      if (b >= BINS) continue;
+      uint64_t excl = 0;
+      if (!first) {
+        excl = look_back(a, tile, first_tile, (uint32_t)b, BINS, epoch);
+        st_status(strow + b, ST_INC | ep | ((excl + tot[q]) & ST_VAL));
+      }
+      // global position of staged element k of bin b = gbase[b] + k
+      sm.gbase[b] = bbase[b] + excl - bstart[q];
+    }
   }
   __syncthreads();
   for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
