@@ -555,15 +555,20 @@ int snn_calibrate(snn_ctx* c) {
   UP(d_projs, dp, "projections");
   uint32_t* d_dtab;
   UP(d_dtab, dtab, "delay and gap tables");
-  // delay guide tables for the finalize step: cell k counts the thresholds <= k << 24
-  std::vector<uint8_t> dguide((size_t)P * kDelayGuideCells, 0);
+  // delay guide tables for the finalize step: cell k covers the words [lo, hi] with
+  // lo = k << (32 - bits); its entry counts the thresholds <= lo, with bit 15 set when
+  // the count at hi is the same (no threshold inside the cell)
+  std::vector<uint16_t> dguide((size_t)P * kDelayGuideCells, 0);
   for (uint32_t i = 0; i < P; ++i) {
-    const ProjSpec& s = c->projs[i];
-    for (uint32_t k = 0; k < kDelayGuideCells; ++k)
-      dguide[(size_t)i * kDelayGuideCells + k] =
-          (uint8_t)(std::upper_bound(s.d_thr.begin(), s.d_thr.end(), k << 24) - s.d_thr.begin());
+    const auto& thr = c->projs[i].d_thr;
+    for (uint32_t k = 0; k < kDelayGuideCells; ++k) {
+      const uint32_t lo = k << (32 - kDelayGuideBits), hi = lo + ((1u << (32 - kDelayGuideBits)) - 1);
+      const uint32_t n_lo = (uint32_t)(std::upper_bound(thr.begin(), thr.end(), lo) - thr.begin());
+      const uint32_t n_hi = (uint32_t)(std::upper_bound(thr.begin(), thr.end(), hi) - thr.begin());
+      dguide[(size_t)i * kDelayGuideCells + k] = (uint16_t)(n_lo | (n_lo == n_hi ? 0x8000u : 0u));
+    }
   }
-  uint8_t* d_dguide;
+  uint16_t* d_dguide;
   UP(d_dguide, dguide, "delay guide tables");
   std::vector<uint32_t> ft_proj, pb_proj;
   std::vector<uint64_t> ft_tile_first(1, 0), pb_t_first(1, 0);

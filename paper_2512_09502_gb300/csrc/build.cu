@@ -956,8 +956,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
       if (P.d_kind == 1) {
         const uint32_t* thr = a.dtables + P.d_tbl_off;
         if (a.dguide) {
-          dk = a.dguide[(uint64_t)p * kDelayGuideCells + (b.y >> 24)];
-          while (dk < P.d_tbl_len && thr[dk] <= b.y) ++dk;
+          const uint32_t e = a.dguide[(uint64_t)p * kDelayGuideCells + (b.y >> (32 - kDelayGuideBits))];
+          dk = e & 0x7FFFu;
+          if (!(e >> 15))
+            while (dk < P.d_tbl_len && thr[dk] <= b.y) ++dk;
         } else {
           dk = upper_bound_u32(thr, P.d_tbl_len, b.y);
         }

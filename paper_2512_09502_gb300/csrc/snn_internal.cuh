@@ -146,9 +146,11 @@ struct BuildArgs {
   const DevBlock* blocks; uint32_t nblocks; uint64_t n_gen_tiles;
   const DevProj* projs; uint32_t nproj;
   const uint32_t* dtables;
-  // per projection, kDelayGuideCells counts #{i : thr[i] <= cell << 24} of its delay table
-  // (Chen & Asau's guide table), or null: finalize then searches the table itself
-  const uint8_t* dguide;
+  // per projection, kDelayGuideCells entries of its delay table's guide (Chen & Asau's
+  // indexed search): the low 15 bits count #{i : thr[i] <= cell start}, bit 15 says that
+  // no threshold falls inside the cell (the count is the answer); null: finalize then
+  // searches the table itself
+  const uint16_t* dguide;
   Geom g;
   uint64_t* rec_a; uint64_t* rec_b;
   uint64_t* hist;           // [R][passes][bins]
@@ -176,7 +178,8 @@ struct BuildArgs {
   uint8_t pass_shift[8], pass_bits[8];
 };
 constexpr uint32_t kHistStride = 1024;     // bins of the widest (10-bit) digit
-constexpr uint32_t kDelayGuideCells = 256;  // guide cells: the top 8 bits of the uniform word
+constexpr uint32_t kDelayGuideBits = 10;    // guide cells: the top 10 bits of the uniform word
+constexpr uint32_t kDelayGuideCells = 1u << kDelayGuideBits;
 
 // counted generation (fixed total over several ranks; pairwise Bernoulli): the
 // records of such a projection land in (rank, projection) blocks whose sizes are
