@@ -119,12 +119,13 @@ class Clocks:
 # source file and its sha256[:16] at capture time; profiles/traffic_balanced_500k.md
 # gives the commands and the raw figures.
 TRAFFIC = {
-    "deliver_kernel": {"bytes_per_unit": 23.07, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
+    "deliver_kernel": {"bytes_per_unit": 23.28, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
     # taken on step_update_kernel, the overlapped form with the same per-neuron loads and stores
-    "update_kernel": {"bytes_per_unit": 15.70, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
-    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
-    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
-    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "source_sha": "723bab21f1a856a4"},
+    "update_kernel": {"bytes_per_unit": 15.71, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
+    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
+    # the mean of the 9-bit (17.00) and the 10-bit (17.22) pass
+    "onesweep_pass": {"bytes_per_unit": 17.11, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
+    "finalize_kernel": {"bytes_per_unit": 17.09, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
 }
 
 
