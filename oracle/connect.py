@@ -50,8 +50,10 @@ def counter_space(pr) -> int:
         return int(pr.rule.param) * pr.n_tgt
     if pr.rule.kind == "fixed_total":
         return int(pr.rule.param)
-    if pr.rule.kind in ("pairwise_bernoulli", "pairwise_bernoulli_geometric"):
+    if pr.rule.kind in ("pairwise_bernoulli", "pairwise_bernoulli_geometric", "all_to_all"):
         return pr.n_tgt * pr.n_src
+    if pr.rule.kind == "one_to_one":
+        return pr.n_tgt
     raise ValueError(pr.rule.kind)
 
 
@@ -82,6 +84,21 @@ def projection_synapses(net, pid: int, counters=None):
         b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
         src = pr.src_first + pr.src_stride * sm.uniform_index(b[0], pr.n_src).astype(np.int64)
         tgt = pr.tgt_first + pr.tgt_stride * t_local
+    elif kind == "one_to_one":
+        # target i connects from source i (the two sets have the same size); counter c = i
+        if pr.n_src != pr.n_tgt:
+            raise ValueError("one-to-one needs as many sources as targets")
+        c = np.arange(pr.n_tgt, dtype=np.uint64) if counters is None else np.asarray(counters, np.uint64)
+        b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
+        src = pr.src_first + pr.src_stride * c.astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * c.astype(np.int64)
+    elif kind == "all_to_all":
+        # every (target i_t, source i_s) pair once, counter c = i_t n_src + i_s
+        c = (np.arange(pr.n_tgt * pr.n_src, dtype=np.uint64) if counters is None
+             else np.asarray(counters, np.uint64))
+        b = ph.stream(c, pid, ph.PURPOSE_SYNAPSE, pr.seed)
+        src = pr.src_first + pr.src_stride * (c % np.uint64(pr.n_src)).astype(np.int64)
+        tgt = pr.tgt_first + pr.tgt_stride * (c // np.uint64(pr.n_src)).astype(np.int64)
     elif kind == "fixed_total":
         N = int(pr.rule.param)
         c = np.arange(N, dtype=np.uint64) if counters is None else np.asarray(counters, np.uint64)

@@ -70,6 +70,10 @@ def expected_per_source(pr, n_tgt_on=None) -> float:
     (fixed in-degree), N n_on / (n_tgt n_src) (fixed total, N spread uniformly over
     the targets), p n_on (pairwise Bernoulli)."""
     n_on = pr.n_tgt if n_tgt_on is None else int(n_tgt_on)
+    if pr.rule.kind in ("one_to_one", "all_to_all"):
+        # rules that use every source of the call need no flagging decision: the
+        # flagged images are the used ones (Methods, "Remote connections")
+        return 0.0
     if pr.rule.kind == "fixed_indegree":
         return pr.rule.param * n_on / pr.n_src
     if pr.rule.kind == "fixed_total":

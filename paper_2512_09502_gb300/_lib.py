@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libsnn.so")
 SNN_OK = 0
 SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_ETIMEOUT, SNN_ESTATE, SNN_EOVERFLOW = -1, -2, -3, -4, -5, -6
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE", -6: "EOVERFLOW"}
-RULES = {"fixed_indegree": 0, "fixed_total": 1, "pairwise_bernoulli": 2, "pairwise_bernoulli_geometric": 3}
+RULES = {"fixed_indegree": 0, "fixed_total": 1, "pairwise_bernoulli": 2, "pairwise_bernoulli_geometric": 3,
+         "one_to_one": 4, "all_to_all": 5}
 W_KINDS = {"const": 0, "normal_sign": 1}
 D_KINDS = {"const": 0, "normal_min": 1}
 WEIGHT_FORMATS = {"f32": 0, "bf16": 1, "f16": 2}

@@ -27,6 +27,8 @@ RULE_FIXED_INDEGREE = "fixed_indegree"
 RULE_FIXED_TOTAL = "fixed_total"
 RULE_PAIRWISE_BERNOULLI = "pairwise_bernoulli"
 RULE_PAIRWISE_BERNOULLI_GEOMETRIC = "pairwise_bernoulli_geometric"
+RULE_ONE_TO_ONE = "one_to_one"                 # target i <- source i (n_src == n_tgt); param unused
+RULE_ALL_TO_ALL = "all_to_all"                 # every source onto every target; param unused
 
 # weight distributions
 W_CONST = "const"
@@ -125,6 +127,10 @@ class Network:
                 tot += int(pr.rule.param) * pr.n_tgt
             elif pr.rule.kind == RULE_FIXED_TOTAL:
                 tot += int(pr.rule.param)
+            elif pr.rule.kind == RULE_ONE_TO_ONE:
+                tot += pr.n_tgt
+            elif pr.rule.kind == RULE_ALL_TO_ALL:
+                tot += pr.n_src * pr.n_tgt
             else:
                 return None
         return tot

@@ -1,5 +1,6 @@
 """Pins of the oracle's connection rules (no GPU)."""
 import numpy as np
+import pytest
 from scipy import stats
 
 from oracle import connect as oc
@@ -148,3 +149,40 @@ def test_geometric_and_pairwise_bernoulli_totals_agree():
     sd = np.sqrt(n_src * n_tgt * p * (1 - p))
     for tot in (tot_g, tot_p):
         assert abs(tot - n_src * n_tgt * p) < 4 * sd
+
+
+def test_all_to_all_is_pairwise_bernoulli_at_p1():
+    """All-to-all makes every (target, source) pair once, in (target, source) order, with
+    the synapse counter i_t n_src + i_s: exactly the pairs, delays and weights of the
+    pairwise Bernoulli rule at p = 1, whose pairs come through its own test stream."""
+    pops = [wl.Population(37), wl.Population(23)]
+    w, d = wl.Dist(wl.W_NORMAL_SIGN, 40.0, 8.0), wl.DELAY_NORMAL
+    a2a = wl.Network("a2a", pops, [wl.Projection(0, 37, 37, 23, wl.Rule(wl.RULE_ALL_TO_ALL, 0), w, d, 9)])
+    pb1 = wl.Network("pb1", pops, [wl.Projection(0, 37, 37, 23, wl.Rule(wl.RULE_PAIRWISE_BERNOULLI, 1.0), w, d, 9)])
+    x, y = oc.generate(a2a), oc.generate(pb1)
+    assert len(x["src"]) == 37 * 23
+    for k in ("src", "tgt", "d", "w", "c"):
+        np.testing.assert_array_equal(x[k], y[k])
+    pairs = set(zip(x["src"].tolist(), x["tgt"].tolist()))
+    assert pairs == {(s, 37 + t) for s in range(37) for t in range(23)}
+    assert a2a.n_synapses_fixed() == 37 * 23
+
+
+def test_one_to_one_pairs_and_draws():
+    """One-to-one connects target i from source i, once each.  Its counter is the target
+    index, so its delays and weights are those of fixed in-degree K = 1 from a single
+    source neuron (counter i_t K + k = i_t), generated by the other rule's code."""
+    n = 150
+    pops = [wl.Population(n), wl.Population(n), wl.Population(1)]
+    w, d = wl.Dist(wl.W_NORMAL_SIGN, -30.0, 6.0), wl.DELAY_NORMAL
+    one = wl.Network("o2o", pops, [wl.Projection(0, n, n, n, wl.Rule(wl.RULE_ONE_TO_ONE, 0), w, d, 4)])
+    fi1 = wl.Network("fi1", pops, [wl.Projection(2 * n, 1, n, n, wl.Rule(wl.RULE_FIXED_INDEGREE, 1), w, d, 4)])
+    x, y = oc.generate(one), oc.generate(fi1)
+    np.testing.assert_array_equal(x["src"], np.arange(n))
+    np.testing.assert_array_equal(x["tgt"], n + np.arange(n))
+    np.testing.assert_array_equal(y["src"], np.full(n, 2 * n))
+    for k in ("tgt", "d", "w", "c"):
+        np.testing.assert_array_equal(x[k], y[k])
+    bad = wl.Network("bad", pops, [wl.Projection(0, n, n, n - 1, wl.Rule(wl.RULE_ONE_TO_ONE, 0), w, d, 4)])
+    with pytest.raises(ValueError):
+        oc.generate(bad)
