@@ -55,6 +55,12 @@ extern "C" {
 /* param = p: each pair kept with probability p, drawn as geometric gaps between kept
    sources (one draw per kept pair instead of one test per pair; p >= ~5e-6) */
 #define SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC 3
+/* Rules that use every source: one-to-one (target i from source i; needs n_src == n_tgt;
+   counter i) and all-to-all (every pair once; counter i_t n_src + i_s).  param is
+   ignored.  The threshold xi does not apply to them: they use every source of the
+   call, so no flagging decision is taken (Methods, "Remote connections"). */
+#define SNN_RULE_ONE_TO_ONE 4
+#define SNN_RULE_ALL_TO_ALL 5
 
 #define SNN_W_CONST 0        /* weight = mean                                          */
 #define SNN_W_NORMAL_SIGN 1  /* normal(mean, sd), clamped at 0 to keep mean's sign    */

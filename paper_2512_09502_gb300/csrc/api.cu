@@ -53,6 +53,7 @@ struct DriveSpec {
 // "Remote connections": K_in N_target / N_source for fixed in-degree, N_target the
 // targets on the target process).
 double per_source(const ProjSpec& s, uint64_t n_on) {
+  if (s.rule.kind == SNN_RULE_ONE_TO_ONE || s.rule.kind == SNN_RULE_ALL_TO_ALL) return 0.0;   // no decision
   if (s.rule.kind == SNN_RULE_FIXED_INDEGREE) return s.rule.param * (double)n_on / s.n_src;
   if (s.rule.kind == SNN_RULE_FIXED_TOTAL) return s.rule.param * (double)n_on / ((double)s.n_tgt * s.n_src);
   return s.rule.param * (double)n_on;                 // pairwise Bernoulli (both variants)
@@ -311,12 +312,21 @@ int gap_table(double p, std::vector<uint32_t>* thr) {
   return SNN_OK;
 }
 
+// rules generated in the fixed in-degree shape (K records per target, counter i_t K + k)
+bool fixed_indegree_shape(const ProjSpec& p) {
+  return p.rule.kind == SNN_RULE_FIXED_INDEGREE || p.rule.kind == SNN_RULE_ONE_TO_ONE ||
+         p.rule.kind == SNN_RULE_ALL_TO_ALL;
+}
+uint64_t indegree_of(const ProjSpec& p) {
+  if (p.rule.kind == SNN_RULE_ONE_TO_ONE) return 1;
+  if (p.rule.kind == SNN_RULE_ALL_TO_ALL) return p.n_src;
+  return (uint64_t)p.rule.param;
+}
+
 uint64_t counter_space(const ProjSpec& p) {
-  switch (p.rule.kind) {
-    case SNN_RULE_FIXED_INDEGREE: return (uint64_t)p.rule.param * p.n_tgt;
-    case SNN_RULE_FIXED_TOTAL: return (uint64_t)p.rule.param;
-    default: return (uint64_t)p.n_tgt * p.n_src;
-  }
+  if (fixed_indegree_shape(p)) return indegree_of(p) * p.n_tgt;
+  if (p.rule.kind == SNN_RULE_FIXED_TOTAL) return (uint64_t)p.rule.param;
+  return (uint64_t)p.n_tgt * p.n_src;
 }
 
 }  // namespace
@@ -409,6 +419,12 @@ static int add_projection(snn_ctx* c, uint32_t src_first, uint32_t n_src, uint32
       if (rule->param > 0 && gap_table(rule->param, &p.g_thr) != SNN_OK)
         return fail(c, SNN_EINVAL, "connection probability too small for the gap table");
       break;
+    case SNN_RULE_ONE_TO_ONE:
+      if (n_src != n_tgt) return fail(c, SNN_EINVAL, "one-to-one needs as many sources as targets");
+      break;
+    case SNN_RULE_ALL_TO_ALL:
+      if ((uint64_t)n_src * n_tgt >= (1ull << 50)) return fail(c, SNN_EINVAL, "all-to-all too large");
+      break;
     default:
       return fail(c, SNN_EINVAL, "unknown rule");
   }
@@ -495,15 +511,17 @@ int snn_calibrate(snn_ctx* c) {
     DevProj& d = dp[i];
     d.src_first = s.src_first; d.n_src = s.n_src; d.src_stride = s.src_stride;
     d.tgt_first = s.tgt_first; d.n_tgt = s.n_tgt; d.tgt_stride = s.tgt_stride;
-    d.rule = (uint32_t)s.rule.kind; d.proj_id = i; d.seed = s.seed;
-    d.K = s.rule.kind == SNN_RULE_FIXED_INDEGREE ? (uint64_t)s.rule.param : 0;
+    d.rule = fixed_indegree_shape(s) ? kRuleFixedIndegree : (uint32_t)s.rule.kind;
+    d.src_mode = s.rule.kind == SNN_RULE_ALL_TO_ALL ? kSrcAll : (s.rule.kind == SNN_RULE_ONE_TO_ONE ? kSrcOneToOne : 0u);
+    d.proj_id = i; d.seed = s.seed;
+    d.K = fixed_indegree_shape(s) ? indegree_of(s) : 0;
     d.N = s.rule.kind == SNN_RULE_FIXED_TOTAL ? (uint64_t)s.rule.param : 0;
     d.pb_thr = (s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI || s.rule.kind == SNN_RULE_PAIRWISE_BERNOULLI_GEOMETRIC)
                    ? (uint64_t)std::floor(s.rule.param * 4294967296.0) : 0;
     d.cbase = ctot; d.csize = counter_space(s);
     c->cbase[i] = ctot;
     ctot += d.csize;
-    d.magic_div = s.rule.kind == SNN_RULE_FIXED_INDEGREE ? magic_for(d.K) : magic_for(d.n_src);
+    d.magic_div = fixed_indegree_shape(s) ? magic_for(d.K) : magic_for(d.n_src);
     d.w_kind = s.w.kind == SNN_W_CONST ? 0 : 1;
     d.w_mean = (float)s.w.mean; d.w_sd = (float)s.w.sd;
     d.d_kind = s.d.kind == SNN_D_CONST ? 0 : 1;
@@ -657,7 +675,7 @@ int snn_calibrate(snn_ctx* c) {
       if (ti0 < 0) continue;
       b.ti0 = (uint32_t)ti0; b.tstep = period;
       b.n_t = (uint32_t)((s.n_tgt - 1 - (uint32_t)ti0) / period + 1);
-      b.count = s.rule.kind == SNN_RULE_FIXED_INDEGREE ? (uint64_t)b.n_t * (uint64_t)s.rule.param
+      b.count = fixed_indegree_shape(s) ? (uint64_t)b.n_t * indegree_of(s)
                                                      : (uint64_t)s.rule.param;
       if (b.count == 0) continue;
       b.out_base = pos;

@@ -233,9 +233,14 @@ __global__ void source_flags(const DevProj* projs, uint32_t nproj, const uint64_
     const uint64_t c = x - P.cbase;
     uint32_t src, tgt;
     if (P.rule == kRuleFixedIndegree) {
-      const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
-      src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
-      tgt = P.tgt_first + (uint32_t)div_magic(c, P.K, P.magic_div) * P.tgt_stride;
+      const uint64_t ti = div_magic(c, P.K, P.magic_div);
+      if (P.src_mode == 0) {
+        const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
+        src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
+      } else {                     // all-to-all: source k = c - ti K; one-to-one: source ti
+        src = P.src_first + (uint32_t)(P.src_mode == kSrcAll ? c - ti * P.K : ti) * P.src_stride;
+      }
+      tgt = P.tgt_first + (uint32_t)ti * P.tgt_stride;
     } else if (P.rule == kRuleFixedTotal) {
       const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
       const uint4 bt = philox_stream(c, P.proj_id, kPurposeFtTarget, P.seed);

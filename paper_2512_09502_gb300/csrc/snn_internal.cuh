@@ -28,6 +28,8 @@ constexpr uint32_t kRuleFixedIndegree = 0;
 constexpr uint32_t kRuleFixedTotal = 1;
 constexpr uint32_t kRulePairwiseBernoulli = 2;
 constexpr uint32_t kRuleBernoulliGeometric = 3;   // pairwise Bernoulli by geometric gaps
+// all-to-all and one-to-one run as fixed in-degree (K = n_src, K = 1) with a fixed source
+constexpr uint32_t kSrcAll = 1, kSrcOneToOne = 2;
 
 // device error word bits
 constexpr uint32_t kErrTimeout = 1u;
@@ -81,6 +83,8 @@ struct DevProj {
   uint32_t src_first, n_src, src_stride;
   uint32_t tgt_first, n_tgt, tgt_stride;
   uint32_t rule, proj_id;
+  uint32_t src_mode;        // fixed in-degree shape: 0 random source, kSrcAll (source = k),
+  uint32_t src_pad;         // kSrcOneToOne (source = target index)
   uint64_t K, N;            // fixed in-degree K / fixed total N
   uint64_t pb_thr;          // Bernoulli threshold (<= 2^32)
   uint64_t cbase, csize;    // global counter base and size

@@ -33,9 +33,10 @@ def update_500k():
 
 
 def construction_112m():
-    """100k neurons, in-degree 900 + 225: 112.5M synapses (about 1.9 GB at peak)."""
+    """300k neurons, in-degree 300 + 75: 112.5M synapses (about 2 GB at peak), sorted on
+    a 19-bit key like the 500k network's (a 9- and a 10-bit pass)."""
     from . import workloads as wl
-    net = wl.balanced(80000, 20000, 900, 225, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0)
+    net = wl.balanced(240000, 60000, 300, 75, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0)
     ctx = _ctx(net, radix_bits=10, sort_items=16, deliver_ctas_per_sm=16)
     ctx.calibrate()
     s = ctx.stats()

@@ -122,3 +122,52 @@ def test_multi_area_over_ranks():
             if sig != tau:
                 np.testing.assert_array_equal(ctx.get_maps(tau, sig, "R"), ref["ranks"][tau]["R"][sig])
                 np.testing.assert_array_equal(ctx.get_maps(tau, sig, "S"), ref["S"][sig][tau])
+
+
+def _every_rule_net(R):
+    """One projection of every rule, including one-to-one and all-to-all, on four
+    populations of uneven sizes."""
+    pops = [wl.Population(n) for n in (211, 211, 57, 90)]
+    w, d = wl.Dist(wl.W_NORMAL_SIGN, 40.0, 8.0), wl.DELAY_NORMAL
+    P = wl.Projection
+    projs = [P(0, 211, 211, 211, wl.Rule(wl.RULE_ONE_TO_ONE, 0), w, d, 3),
+             P(422, 57, 479, 90, wl.Rule(wl.RULE_ALL_TO_ALL, 0), w, d, 4),
+             P(0, 211, 422, 57, wl.Rule(wl.RULE_FIXED_INDEGREE, 5), w, d, 5),
+             P(211, 211, 0, 211, wl.Rule(wl.RULE_FIXED_TOTAL, 900), w, d, 6),
+             P(479, 90, 211, 211, wl.Rule(wl.RULE_PAIRWISE_BERNOULLI, 0.05), w, d, 7),
+             P(211, 211, 479, 90, wl.Rule(wl.RULE_ALL_TO_ALL, 0), w, d, 8)]
+    return wl.Network("every_rule", pops, projs, n_ranks=R)
+
+
+@pytest.mark.parametrize("R,xi", [(1, 0.0), (4, 0.0), (5, 1.0)])
+def test_one_to_one_and_all_to_all(R, xi):
+    """One-to-one and all-to-all beside the other rules: layouts bit-exact and every map
+    equal to the oracle's on one and several ranks (xi applies to the random rules only)."""
+    net = _every_rule_net(R)
+    ctx = gpu_build(net, xi=xi)
+    _, ref = oracle_layout(net, xi=xi)
+    for tau in range(R):
+        compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
+    if R > 1:
+        compare_maps(ctx, ref, R)
+    n_pb = sum(int(np.sum(r["src"] >= 479)) for r in ref["ranks"])       # the Bernoulli block's sources
+    assert ctx.stats()["n_synapses"] == 211 + 57 * 90 + 5 * 57 + 900 + n_pb + 211 * 90
+    ctx.destroy()
+
+
+def test_one_to_one_and_all_to_all_dry_run():
+    """Uncounted rules only (fixed in-degree, one-to-one, all-to-all): a dry run of rank 2
+    of 4 builds that rank's rows and R/L maps of the full build."""
+    pops = [wl.Population(n) for n in (300, 300, 40)]
+    w, d = wl.Dist(wl.W_NORMAL_SIGN, 40.0, 8.0), wl.DELAY_NORMAL
+    P = wl.Projection
+    net = wl.Network("uncounted", pops, [P(0, 300, 300, 300, wl.Rule(wl.RULE_ONE_TO_ONE, 0), w, d, 3),
+                                         P(600, 40, 0, 300, wl.Rule(wl.RULE_ALL_TO_ALL, 0), w, d, 4),
+                                         P(300, 300, 0, 300, wl.Rule(wl.RULE_FIXED_INDEGREE, 7), w, d, 5)],
+                     n_ranks=4)
+    dry = gpu_build(net, dry_run_rank=2)
+    _, ref = oracle_layout(net)
+    compare_rank(dry.get_connections(2), ref["ranks"][2])
+    for sig in (0, 1, 3):
+        np.testing.assert_array_equal(dry.get_maps(2, sig, "R"), ref["ranks"][2]["R"][sig])
+        np.testing.assert_array_equal(dry.get_maps(2, sig, "L"), ref["ranks"][2]["L"][sig])
