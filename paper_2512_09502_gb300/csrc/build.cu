@@ -841,6 +841,14 @@ __device__ __forceinline__ float draw_weight(const DevProj& P, uint32_t w2, uint
 
 constexpr int FIN_Q = 4;   // consecutive records per thread of the finalize kernel
 
+// Target of draw c of a fixed-total projection.  Out of line: the finalize loop is
+// unrolled over its records and would otherwise hold eight copies of this Philox block
+// in its instruction footprint, for a path that fixed in-degree records never take.
+__device__ __noinline__ uint32_t fixed_total_target(const DevProj& Q, uint64_t c) {
+  const uint4 bt = philox_stream(c, Q.proj_id, kPurposeFtTarget, Q.seed);
+  return Q.tgt_first + uniform_index(bt.x, Q.n_tgt) * Q.tgt_stride;
+}
+
 // Each thread decodes FIN_Q consecutive sorted records: one pair of 16-byte loads, the
 // projection lookup reused while the counters stay in one projection, and one vector
 // store per output array.  Row starts: a record whose row differs from its
@@ -932,8 +940,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
           t = Q.tgt_first + (uint32_t)ti * Q.tgt_stride;
         } else {                       // fixed total on one rank: the draw index
           c = l;
-          const uint4 bt = philox_stream(c, Q.proj_id, kPurposeFtTarget, Q.seed);
-          t = Q.tgt_first + uniform_index(bt.x, Q.n_tgt) * Q.tgt_stride;
+          t = fixed_total_target(Q, c);
         }
       } else {
         if (cidx - p_lo >= p_hi - p_lo) {
@@ -946,8 +953,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
         if (Q.rule == kRuleFixedIndegree) {
           t = Q.tgt_first + (uint32_t)div_magic(c, Q.K, Q.magic_div) * Q.tgt_stride;
         } else if (Q.rule == kRuleFixedTotal) {
-          const uint4 bt = philox_stream(c, Q.proj_id, kPurposeFtTarget, Q.seed);
-          t = Q.tgt_first + uniform_index(bt.x, Q.n_tgt) * Q.tgt_stride;
+          t = fixed_total_target(Q, c);
         } else {
           t = Q.tgt_first + (uint32_t)div_magic(c, Q.n_src, Q.magic_div) * Q.tgt_stride;
         }
