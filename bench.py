@@ -116,27 +116,46 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of full-size one-pass
 # ncu captures of the timed step, divided by the units the launches processed), with the
-# source file and its sha256[:16] at capture time; profiles/traffic_balanced_500k.md
-# gives the commands and the raw figures.
+# kernel whose source text was measured (file, function, sha256[:16] of the function's
+# text at capture time); profiles/traffic_balanced_500k.md gives the commands and the
+# raw figures.
 TRAFFIC = {
-    "deliver_kernel": {"bytes_per_unit": 23.28, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
+    "deliver_kernel": {"bytes_per_unit": 23.28, "source": "sim.cu", "function": "deliver_kernel",
+                       "function_sha": "b3ca0bf24329b8ff"},
     # taken on step_update_kernel, the overlapped form with the same per-neuron loads and stores
-    "update_kernel": {"bytes_per_unit": 15.71, "source": "sim.cu", "source_sha": "1dc565be6e7c2fb7"},
-    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
+    "update_kernel": {"bytes_per_unit": 15.71, "source": "sim.cu", "function": "step_update_kernel",
+                      "function_sha": "9ea0313c697d5f62"},
+    "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "function": "gen_kernel",
+                   "function_sha": "25cc3b498afc3f35"},
     # the mean of the 9-bit (17.00) and the 10-bit (17.22) pass
-    "onesweep_pass": {"bytes_per_unit": 17.11, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
-    "finalize_kernel": {"bytes_per_unit": 17.09, "source": "build.cu", "source_sha": "de3e29662f7f1471"},
+    "onesweep_pass": {"bytes_per_unit": 17.11, "source": "build.cu", "function": "onesweep_pass",
+                      "function_sha": "61cc3760491b97d0"},
+    "finalize_kernel": {"bytes_per_unit": 17.09, "source": "build.cu", "function": "finalize_kernel",
+                        "function_sha": "3ca9c3e9d488b2b7"},
 }
 
 
+def kernel_text_sha(path: str, function: str) -> str:
+    """sha256[:16] of a kernel's definition: from its __global__ line to the closing brace
+    at column 0."""
+    lines = open(path).read().split("\n")
+    for i, line in enumerate(lines):
+        if "__global__" in line and (" " + function + "(") in line:
+            j = i
+            while j < len(lines) and lines[j] != "}":
+                j += 1
+            return hashlib.sha256("\n".join(lines[i:j + 1]).encode()).hexdigest()[:16]
+    return ""
+
+
 def traffic_of(kernel: str, units_per_launch: float):
-    """Measured DRAM bytes per launch, when the figure was taken on the current kernel
-    source; else None."""
+    """Measured DRAM bytes per launch, when the figure was taken on the kernel's current
+    source text; else None."""
     d = TRAFFIC.get(kernel)
     if not d:
         return None
     src = os.path.join(ROOT, "paper_2512_09502_gb300", "csrc", d["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+    if kernel_text_sha(src, d["function"]) != d["function_sha"]:
         return None
     return d["bytes_per_unit"] * units_per_launch
 
