@@ -120,18 +120,18 @@ class Clocks:
 # text at capture time); profiles/traffic_balanced_500k.md gives the commands and the
 # raw figures.
 TRAFFIC = {
-    "deliver_kernel": {"bytes_per_unit": 23.28, "source": "sim.cu", "function": "deliver_kernel",
+    "deliver_kernel": {"bytes_per_unit": 23.24, "source": "sim.cu", "function": "deliver_kernel",
                        "function_sha": "b3ca0bf24329b8ff"},
     # taken on step_update_kernel, the overlapped form with the same per-neuron loads and stores
     "update_kernel": {"bytes_per_unit": 15.71, "source": "sim.cu", "function": "step_update_kernel",
                       "function_sha": "9ea0313c697d5f62"},
     "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "function": "gen_kernel",
-                   "function_sha": "25cc3b498afc3f35"},
+                   "function_sha": "c509c81f4a7a4b1b"},
     # the mean of the 9-bit (17.00) and the 10-bit (17.22) pass
     "onesweep_pass": {"bytes_per_unit": 17.11, "source": "build.cu", "function": "onesweep_pass",
                       "function_sha": "61cc3760491b97d0"},
     "finalize_kernel": {"bytes_per_unit": 17.09, "source": "build.cu", "function": "finalize_kernel",
-                        "function_sha": "3ca9c3e9d488b2b7"},
+                        "function_sha": "165501cd1dfda545"},
 }
 
 
