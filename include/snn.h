@@ -117,7 +117,8 @@ typedef struct snn_config {
      of a larger network in the absence of the rest, to estimate memory and construction
      time): with dry_run = 1 and n_ranks > 1, snn_calibrate builds only the connections,
      image rows and R/L maps of rank dry_run_rank, as if n_ranks ranks existed.  Fixed
-     in-degree rules only (EINVAL otherwise); no source-side maps and no simulation state:
+     in-degree, one-to-one and all-to-all rules only (EINVAL otherwise); no source-side
+     maps and no simulation state:
      snn_simulate, snn_get_spikes and snn_get_state return ESTATE, snn_get_connections /
      snn_get_row / snn_get_maps (R, L) answer for that rank only.  0 = off. */
   int32_t dry_run;

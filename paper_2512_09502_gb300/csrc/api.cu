@@ -604,8 +604,8 @@ int snn_calibrate(snn_ctx* c) {
   const bool dry = c->cfg.dry_run != 0;
   const uint32_t dr = dry ? c->cfg.dry_run_rank : 0;
   if (dry && counted)
-    return fail(c, SNN_EINVAL, "a dry run supports the fixed in-degree rule only (the other rules are placed "
-                               "by counting draws over every rank)");
+    return fail(c, SNN_EINVAL, "a dry run supports fixed in-degree, one-to-one and all-to-all only (the other "
+                               "rules are placed by counting draws over every rank)");
   CountedArgs ca{};
   std::vector<uint64_t> ft_tot_h, pb_tot_h;
   std::vector<void*> counted_bufs;
