@@ -15,8 +15,8 @@ Definitions followed (paper, Methods, "Remote connections"):
   expected connections per source on rank tau reach xi, the flagging is skipped there:
   all its sources get an image on tau (``forced_images``); xi <= 0 keeps flagging.
 * Connections are sorted by source as the first key so that one source's outgoing
-  connections are (first index, count) ("GPU memory levels").  The paper names no second
-  key; the sort is stable, so one source's connections keep generation order (gidx).
+  connections are (first index, count) ("GPU memory levels"); the second key is the
+  delay, and ties keep generation order (reading: stable sort, tie-break gidx).
 * Image order (reading): images of tau are ordered by (sigma, s) with sigma ascending,
   L = M_tau + position in that order -- the result RemoteConnect gives when called
   once per source rank in ascending sigma.  The rows of tau are the M_tau local
@@ -105,8 +105,8 @@ def forced_images(net, part, xi: float):
 
 
 def build_rank(syn, part, tau: int, forced=()):
-    """Connections of rank tau, sorted by (local-first source rank, source), ties in
-    generation order.  Returns dict with row_ptr (M_tau + n_img + 1), tgt
+    """Connections of rank tau, sorted by (local-first source rank, source, delay),
+    ties in generation order.  Returns dict with row_ptr (M_tau + n_img + 1), tgt
     (local target index), d, w, src (global), gidx, img_sigma / img_s per image row
     and the R / L maps per source rank.  ``forced`` adds images (sigma, s) without
     connections (the all-sources variant); their rows are empty."""
@@ -117,7 +117,7 @@ def build_rank(syn, part, tau: int, forced=()):
     sigma = rank_of[src]
     s = local_of[src]
     sp = source_slot(sigma, tau)
-    order = np.lexsort((syn["gidx"][sel], s, sp))
+    order = np.lexsort((syn["gidx"][sel], syn["d"][sel], s, sp))
     sel, src, sigma, s, sp = sel[order], src[order], sigma[order], s[order], sp[order]
     local = sp == 0
     local_counts = np.bincount(s[local], minlength=M[tau]).astype(np.int64)

@@ -538,7 +538,8 @@ int snn_calibrate(snn_ctx* c) {
   g.R = R; g.N = N;
   g.rb = R > 1 ? bits_for(R - 1) : 0;
   g.sb = bits_for(maxM - 1);
-  g.key_bits = g.rb + g.sb;
+  g.db = bits_for(dmax);
+  g.key_bits = g.rb + g.sb + g.db;
   g.cbits = std::max(1u, bits_for(ctot ? ctot - 1 : 0));
   g.magic_R = magic_for(R);
   if (g.key_bits + g.cbits > 64 && !c->cfg.dry_run)
@@ -573,21 +574,6 @@ int snn_calibrate(snn_ctx* c) {
   UP(d_projs, dp, "projections");
   uint32_t* d_dtab;
   UP(d_dtab, dtab, "delay and gap tables");
-  // delay guide tables for the finalize step: cell k covers the words [lo, hi] with
-  // lo = k << (32 - bits); its entry counts the thresholds <= lo, with bit 15 set when
-  // the count at hi is the same (no threshold inside the cell)
-  std::vector<uint16_t> dguide((size_t)P * kDelayGuideCells, 0);
-  for (uint32_t i = 0; i < P; ++i) {
-    const auto& thr = c->projs[i].d_thr;
-    for (uint32_t k = 0; k < kDelayGuideCells; ++k) {
-      const uint32_t lo = k << (32 - kDelayGuideBits), hi = lo + ((1u << (32 - kDelayGuideBits)) - 1);
-      const uint32_t n_lo = (uint32_t)(std::upper_bound(thr.begin(), thr.end(), lo) - thr.begin());
-      const uint32_t n_hi = (uint32_t)(std::upper_bound(thr.begin(), thr.end(), hi) - thr.begin());
-      dguide[(size_t)i * kDelayGuideCells + k] = (uint16_t)(n_lo | (n_lo == n_hi ? 0x8000u : 0u));
-    }
-  }
-  uint16_t* d_dguide;
-  UP(d_dguide, dguide, "delay guide tables");
   std::vector<uint32_t> ft_proj, pb_proj;
   std::vector<uint64_t> ft_tile_first(1, 0), pb_t_first(1, 0);
   for (uint32_t i = 0; i < P; ++i) {
@@ -740,7 +726,7 @@ int snn_calibrate(snn_ctx* c) {
 
   a.blocks = d_blocks; a.nblocks = (uint32_t)blocks.size();
   a.n_gen_tiles = tiles;
-  a.projs = d_projs; a.nproj = P; a.dtables = d_dtab; a.dguide = d_dguide; a.g = g;
+  a.projs = d_projs; a.nproj = P; a.dtables = d_dtab; a.g = g;
   a.rec_a = rec_a; a.rec_b = rec_b; a.hist = hist; a.bin_base = bin_base;
   a.seg_start = c->d_seg_start; a.seg_tile0 = d_seg_tile0; a.status = status;
   a.counters = counters; a.err = c->d_err; a.passes = passes; a.radix_bits = RB;
@@ -808,7 +794,6 @@ int snn_calibrate(snn_ctx* c) {
   CK(cudaEventRecord(ev[3], c->st));
   dfree(c, cur);
   dfree(c, d_blocks);
-  dfree(c, d_dguide);
   dfree(c, counters);
   for (void* p : counted_bufs) dfree(c, p);
 

@@ -1,5 +1,5 @@
 // build.cu -- on-device network construction: connection generation, the
-// radix sort by source, and the final per-rank CSR layout.
+// source/delay radix sort, and the final per-rank CSR layout.
 //
 // Paper: Methods, "Creation of the remote connection structures for point-to-point
 // MPI communication" (connections generated in GPU memory from the rule dictionary,
@@ -16,9 +16,9 @@
 //                    warp ranking from digit-bit ballots, shared-memory staging so that each
 //                    digit run is written contiguously, then a decoupled look-back over
 //                    the segment's earlier tiles (bounded spin) for the global offsets;
-//   finalize_kernel  decodes the sorted records: rank-local target, delay and weight
-//                    (regenerated from the counter); writes the SoA arrays and the
-//                    dense row starts (the CSR) from record boundaries.
+//   finalize_kernel  decodes the sorted records: rank-local target, weight
+//                    (regenerated from the counter), delay; writes the SoA arrays and
+//                    the dense row starts (the CSR) from record boundaries.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -41,9 +41,24 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // ---------------------------------------------------------------------------
 // generation
 // ---------------------------------------------------------------------------
+// Inverse of an integer CDF table: #{i : thr[i] <= w}.  The guide table (Chen & Asau's
+// indexed search) holds the count at the start of each 2^24-wide window of w, so the
+// search starts there and needs at most a few compares; the result equals a plain
+// binary search.
+constexpr int GUIDE_BITS = 12;      // guide cells: the top 12 bits of the uniform word
+
+__device__ __forceinline__ uint32_t guided_count(const uint32_t* thr, uint32_t len, const uint8_t* guide,
+                                                 uint32_t w) {
+  uint32_t c = guide[w >> (32 - GUIDE_BITS)];
+  while (c < len && thr[c] <= w) ++c;
+  return c;
+}
+
 __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
+  __shared__ uint32_t s_tbl[256];
+  __shared__ uint8_t s_guide[1 << GUIDE_BITS];
   __shared__ DevBlock s_blk;
   __shared__ DevProj s_proj;
   const int tid = threadIdx.x;
@@ -65,6 +80,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   int cur_rank = -1;
   const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
 
+  uint32_t cur_tbl = 0xFFFFFFFFu;      // delay table staged in s_tbl / s_guide
   for (uint64_t tile = t0; tile < t1; ++tile) {
     __syncthreads();
     if (tid == 0) {
@@ -89,6 +105,15 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       }
       cur_rank = blk.rank;
     }
+    if (P.d_kind == 1 && P.d_tbl_off != cur_tbl) {   // block-uniform: P is shared
+      // stage the delay table and its guide only when the projection's table changes
+      for (uint32_t i = tid; i < P.d_tbl_len; i += GEN_BLOCK) s_tbl[i] = a.dtables[P.d_tbl_off + i];
+      __syncthreads();
+      for (uint32_t cell = tid; cell < (1u << GUIDE_BITS); cell += GEN_BLOCK)
+        s_guide[cell] = (uint8_t)upper_bound_u32(s_tbl, P.d_tbl_len, cell << (32 - GUIDE_BITS));
+      __syncthreads();
+      cur_tbl = P.d_tbl_off;
+    }
 
     const uint64_t e0 = (tile - blk.tile_first) * (uint64_t)GEN_TILE;
     const uint32_t n = (uint32_t)min((uint64_t)GEN_TILE, blk.count - e0);
@@ -107,8 +132,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
       const uint64_t e = e0 + i;
       const uint64_t c = P.rule == kRuleFixedIndegree ? cm + k : e;   // fixed total on one rank: draws
       // the source: word x of the synapse's Philox block, or fixed (all-to-all: k;
-      // one-to-one: the target's index).  The block is drawn either way: a branch here
-      // made the compiler trade the random path's registers (58 -> 32) for 15% more time
+      // one-to-one: the target's index); the delay: word y
       const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id,
                                                kPurposeSynapse), key);
       const uint32_t si = P.src_mode == 0 ? uniform_index(b.x, P.n_src)
@@ -120,7 +144,9 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
         sig = src - s * g.R;
       }
       const uint32_t slot = sig == blk.rank ? 0u : (sig < blk.rank ? sig + 1 : sig);
-      const uint64_t kk = ((uint64_t)slot << g.sb) | s;
+      uint32_t d = P.d_const;
+      if (P.d_kind == 1) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
+      const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
       const uint64_t cid = a.pos_counters ? blk.out_base + e : P.cbase + c;
       a.rec_a[blk.out_base + e] = (kk << g.cbits) | (cid & cmask);
       if (hist) {
@@ -522,16 +548,18 @@ __device__ __forceinline__ uint32_t rank_of(uint32_t g, uint32_t R, uint64_t mag
   return g - (uint32_t)div_magic(g, R, magic_R) * R;
 }
 
-// record of one synapse with source `src` on target rank `rank`
+// record of one synapse (source src, delay from w1) on target rank `rank`
 __device__ __forceinline__ uint64_t make_record(const DevProj& P, const Geom& g, uint32_t rank, uint64_t c,
-                                                uint32_t src) {
+                                                uint32_t src, uint32_t w1, const uint32_t* tbl) {
   uint32_t sig = 0, s = src;
   if (g.R > 1) {
     s = (uint32_t)div_magic(src, g.R, g.magic_R);
     sig = src - s * g.R;
   }
   const uint32_t slot = sig == rank ? 0u : (sig < rank ? sig + 1 : sig);
-  const uint64_t kk = ((uint64_t)slot << g.sb) | s;
+  uint32_t d = P.d_const;
+  if (P.d_kind == 1) d += upper_bound_u32(tbl, P.d_tbl_len, w1);
+  const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
   const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
   return (kk << g.cbits) | ((P.cbase + c) & cmask);
 }
@@ -649,6 +677,7 @@ __global__ void pb_scan_kernel(CountedArgs c) {
 __global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs a) {
   constexpr int NW = 8, ITEMS = kCountTile / 256;
   __shared__ uint32_t s_w[NW][kMaxCountedRanks / 4 * 4];
+  __shared__ uint32_t s_tbl[256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1;
   const uint32_t nb = 32 - __clz(c.R);        // bits of the values 0 .. R
@@ -658,6 +687,8 @@ __global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs 
     const uint32_t q = upper_bound_u64(c.ft_tile_first, c.n_ft, tile) - 1;
     const uint32_t pid = c.ft_proj[q];
     const DevProj& P = c.projs[pid];
+    if (P.d_kind == 1)
+      for (uint32_t i = tid; i < P.d_tbl_len; i += 256) s_tbl[i] = a.dtables[P.d_tbl_off + i];
     __syncthreads();
     const uint64_t j0 = (tile - c.ft_tile_first[q]) * kCountTile;
     const uint32_t n = (uint32_t)min((uint64_t)kCountTile, P.N - j0);
@@ -674,7 +705,7 @@ __global__ void __launch_bounds__(256) ft_place_kernel(CountedArgs c, BuildArgs 
         const uint32_t t = P.tgt_first + uniform_index(bt.x, P.n_tgt) * P.tgt_stride;
         rk[j] = rank_of(t, c.R, c.magic_R);
         const uint32_t src = P.src_first + uniform_index(b.x, P.n_src) * P.src_stride;
-        rec[j] = make_record(P, a.g, rk[j], cc, src);
+        rec[j] = make_record(P, a.g, rk[j], cc, src, b.y, s_tbl);
       }
       // peers (same target rank) from one ballot per bit of the rank (R marks no draw)
       const uint32_t key = rk[j] == 0xFFFFFFFFu ? c.R : rk[j];
@@ -733,9 +764,10 @@ __global__ void __launch_bounds__(256) pb_place_kernel(CountedArgs c, BuildArgs 
         geometric_walk(P, c.tables + P.g_tbl_off, ti, [&](uint32_t s, bool keep, uint32_t m, uint32_t r) {
           if (keep) {
             const uint64_t qq = ti * P.n_src + s;
+            const uint4 b = philox_stream(qq, P.proj_id, kPurposeSynapse, P.seed);
             const uint32_t src = P.src_first + s * P.src_stride;
             const uint64_t at = pos + r;
-            const uint64_t rr = make_record(P, a.g, rank, qq, src);
+            const uint64_t rr = make_record(P, a.g, rank, qq, src, b.y, a.dtables + P.d_tbl_off);
             if (at < end) a.rec_a[at] = rr; else atomicOr(a.err, kErrBounds);
           }
           pos += __popc(m);
@@ -748,9 +780,10 @@ __global__ void __launch_bounds__(256) pb_place_kernel(CountedArgs c, BuildArgs 
       const bool keep = s < P.n_src && (uint64_t)pb_word(P, qq) < P.pb_thr;
       const uint32_t m = __ballot_sync(0xffffffffu, keep);
       if (keep) {
+        const uint4 b = philox_stream(qq, P.proj_id, kPurposeSynapse, P.seed);
         const uint32_t src = P.src_first + s * P.src_stride;
         const uint64_t at = pos + __popc(m & ((1u << lane) - 1));
-        const uint64_t r = make_record(P, a.g, rank, qq, src);
+        const uint64_t r = make_record(P, a.g, rank, qq, src, b.y, a.dtables + P.d_tbl_off);
         if (at < end) a.rec_a[at] = r; else atomicOr(a.err, kErrBounds);
       }
       pos += __popc(m);
@@ -858,6 +891,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
   const Geom g = a.g;
   const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
   const uint64_t smask = (1ull << g.sb) - 1;
+  const uint64_t dmask = (1ull << g.db) - 1;
   const uint64_t nq = (E + FIN_Q - 1) / FIN_Q;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
@@ -879,8 +913,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
     int64_t prow = -1;
     if (i0 > a.seg_start[seg]) {
       const uint64_t kp = rec[i0 - 1] >> g.cbits;
-      const uint32_t ps = (uint32_t)(kp >> g.sb);
-      prow = ps < g.R ? (int64_t)((uint64_t)doff[ps] + (kp & smask)) : (int64_t)g.N;
+      const uint32_t ps = (uint32_t)(kp >> (g.db + g.sb));
+      prow = ps < g.R ? (int64_t)((uint64_t)doff[ps] + ((kp >> g.db) & smask)) : (int64_t)g.N;
     }
     uint32_t p = 0, blk_i = 0;
     uint64_t p_lo = 0, p_hi = 0;   // counters [p_lo, p_hi) of the cached projection p (none yet)
@@ -901,8 +935,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
       }
       const uint64_t key = r[j] >> g.cbits;
       const uint64_t cidx = r[j] & cmask;
-      const uint32_t s = (uint32_t)(key & smask);
-      const uint32_t slot = (uint32_t)(key >> g.sb);
+      const uint32_t d = (uint32_t)(key & dmask);
+      const uint32_t s = (uint32_t)((key >> g.db) & smask);
+      const uint32_t slot = (uint32_t)(key >> (g.db + g.sb));
       const uint64_t row = slot < g.R ? (uint64_t)doff[slot] + s : (uint64_t)g.N;
       if (row >= g.N) {              // corrupt record: flag it, write nothing for it
         atomicOr(a.err, kErrBounds);
@@ -960,22 +995,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
       }
       const DevProj& P = a.projs[p];
       tl[j] = g.R == 1 ? t : (uint32_t)div_magic(t, g.R, g.magic_R);
-      // one Philox block per synapse: word x drew the source, y draws the delay, z and w
-      // the weight
+      dd[j] = d;
       const uint4 b = philox_stream(c, P.proj_id, kPurposeSynapse, P.seed);
-      uint32_t dk = 0;                 // #{i : thr[i] <= b.y}: from the guide cell, then a short scan
-      if (P.d_kind == 1) {
-        const uint32_t* thr = a.dtables + P.d_tbl_off;
-        if (a.dguide) {
-          const uint32_t e = a.dguide[(uint64_t)p * kDelayGuideCells + (b.y >> (32 - kDelayGuideBits))];
-          dk = e & 0x7FFFu;
-          if (!(e >> 15))
-            while (dk < P.d_tbl_len && thr[dk] <= b.y) ++dk;
-        } else {
-          dk = upper_bound_u32(thr, P.d_tbl_len, b.y);
-        }
-      }
-      dd[j] = P.d_const + dk;
       const float w = draw_weight(P, b.z, b.w);
       if (a.w_format == 0) {
         wb[j] = __float_as_uint(w);

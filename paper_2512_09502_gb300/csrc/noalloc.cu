@@ -146,6 +146,7 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   } else {
     NA_FAIL(SNN_EINVAL, "bad delay distribution");
   }
+  const uint32_t dmax = d_smin + (uint32_t)thr.size();
 
   Scratch* sc = nullptr;
   int rc = scratch_address(&sc, msg, mlen);
@@ -154,12 +155,13 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   NA_CK(cudaGetDevice(&dev));
   NA_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
 
-  // geometry of a single rank: key = source
+  // geometry of a single rank: key = (source << db) | delay
   auto bits_for = [](uint64_t v) { uint32_t b = 0; while (b < 64 && (v >> b) != 0) ++b; return b; };
   Geom g{};
   g.R = 1; g.N = n_neurons; g.rb = 0;
   g.sb = bits_for(n_neurons - 1);
-  g.key_bits = g.sb;
+  g.db = bits_for(dmax);
+  g.key_bits = g.sb + g.db;
   g.cbits = std::max(1u, bits_for(E - 1));
   g.magic_R = magic_for(1);
   const uint32_t passes = (g.key_bits + 7) / 8;

@@ -2,15 +2,15 @@
 //
 // Record layout of the construction sort (one uint64 per synapse):
 //     record = key << cbits | cidx
-//     key    = (slot << sb) | s
+//     key    = (slot << (sb + db)) | (s << db) | d
 // slot is the source rank seen from the target rank (0 = local, then the other ranks
-// in ascending order), s the source's rank-local index, and cidx the synapse's global
-// generation counter (projection counter base + projection-local counter).  Sorting by
-// the key with a stable LSD radix sort over records that were written in generation
-// order gives "sorted by source, ties in generation order" (paper, Methods, "GPU memory
-// levels": one source's connections are (first index, count)), and cidx lets the last
-// stage regenerate the target, delay and weight of every synapse from the counter-based
-// generator.
+// in ascending order), s the source's rank-local index, d the delay in steps and
+// cidx the synapse's global generation counter (projection counter base + projection-
+// local counter).  Sorting by the key with a stable LSD radix sort over records that
+// were written in generation order reproduces "sorted by source as first key, then
+// delay, ties in generation order" (paper, Methods, "GPU memory levels": one source's
+// connections are (first index, count)), and cidx lets the last stage regenerate the
+// target and weight of every synapse from the counter-based generator.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -109,8 +109,9 @@ struct DevBlock {
 };
 
 struct Geom {
-  uint32_t R, rb, sb, key_bits, cbits;
+  uint32_t R, rb, sb, db, key_bits, cbits;
   uint32_t N;               // neurons
+  uint32_t pad;
   uint64_t magic_R;         // floor(2^64 / R)
 };
 
@@ -150,11 +151,6 @@ struct BuildArgs {
   const DevBlock* blocks; uint32_t nblocks; uint64_t n_gen_tiles;
   const DevProj* projs; uint32_t nproj;
   const uint32_t* dtables;
-  // per projection, kDelayGuideCells entries of its delay table's guide (Chen & Asau's
-  // indexed search): the low 15 bits count #{i : thr[i] <= cell start}, bit 15 says that
-  // no threshold falls inside the cell (the count is the answer); null: finalize then
-  // searches the table itself
-  const uint16_t* dguide;
   Geom g;
   uint64_t* rec_a; uint64_t* rec_b;
   uint64_t* hist;           // [R][passes][bins]
@@ -182,8 +178,6 @@ struct BuildArgs {
   uint8_t pass_shift[8], pass_bits[8];
 };
 constexpr uint32_t kHistStride = 1024;     // bins of the widest (10-bit) digit
-constexpr uint32_t kDelayGuideBits = 10;    // guide cells: the top 10 bits of the uniform word
-constexpr uint32_t kDelayGuideCells = 1u << kDelayGuideBits;
 
 // counted generation (fixed total over several ranks; pairwise Bernoulli): the
 // records of such a projection land in (rank, projection) blocks whose sizes are

@@ -31,20 +31,23 @@ def test_balanced_5k_bit_exact():
 
 @pytest.mark.parametrize("rb", [8, 9, 10])
 @pytest.mark.parametrize("items", [8, 12, 16])
-@pytest.mark.parametrize("R", [1, 3])
-def test_every_sort_kernel_width(rb, items, R):
-    """Every digit width and tile (8, 12, 16 records per thread) of the radix sort on a
-    19-bit key -- 300,001 neurons with K = 2 + 1: 19 source bits on one rank, 2 slot bits
-    + 17 on three -- sorted in digits of 8, 8, 3 bits (widest digit 8 or 9) or 9, 10 bits
-    (widest 10), over ~110 tiles with a ragged tail, bit-exact against the oracle."""
-    net = wl.balanced(240001, 60000, 2, 1, wl.DELAY_NORMAL, seed=rb * 100 + items, n_ranks=R)
+@pytest.mark.parametrize("n,R,key_bits,passes", [(16001, 1, 20, {8: 3, 9: 3, 10: 2}),
+                                                 (2001, 1, 17, {8: 3, 9: 2, 10: 2}),
+                                                 (48001, 3, 22, {8: 3, 9: 3, 10: 3})])
+def test_every_sort_kernel_width(rb, items, n, R, key_bits, passes):
+    """Every digit width and tile (8, 12, 16 records per thread) of the radix sort on
+    (rank slot, source, delay) keys: 14 source + 6 delay bits (digits 8, 8, 4, or 10, 10
+    when the widest is 10), 11 + 6 bits (8, 8, 1, or 8, 9), and on 3 ranks 2 slot + 14
+    source + 6 delay bits (8, 8, 6), over several tiles with ragged tails, bit-exact
+    against the oracle."""
+    net = wl.balanced(n * 4 // 5, n - n * 4 // 5, 30, 8, wl.DELAY_NORMAL, seed=rb * 100 + items, n_ranks=R)
     ctx = gpu_build(net, radix_bits=rb, sort_items=items)
     syn, ref = oracle_layout(net)
     for tau in range(R):
         compare_rank(ctx.get_connections(tau), ref["ranks"][tau])
     st = ctx.stats()
     assert st["n_synapses"] == len(syn["src"]) and st["radix_bits"] == rb
-    assert st["key_bits"] == 19 and st["sort_passes"] == (2 if rb == 10 else 3)
+    assert st["key_bits"] == key_bits and st["sort_passes"] == passes[rb]
     ctx.destroy()
 
 
@@ -102,7 +105,7 @@ def test_low_precision_weight_formats(fmt):
 def test_full_size_sampled_parity():
     """The scaled balanced network at full size (5.625G synapses): exact totals, exact
     row sums, and sampled targets regenerated by the oracle found in their source
-    rows, in generation order, with identical delay and weight."""
+    rows with identical delay and weight."""
     net = wl.balanced_scaled(1.0)
     ctx = gpu_build(net)
     st = ctx.stats()
@@ -113,11 +116,10 @@ def test_full_size_sampled_parity():
             one = oc.fixed_indegree_target(net, pid, int(t))
             for s in np.unique(one["src"])[:25]:
                 tgt, w, d = ctx.get_row(0, int(s))
-                # one projection per source: generation order c = i_t K + k, so targets
-                # ascend along the row and one target's connections come in k order
-                assert np.all(np.diff(tgt.astype(np.int64)) >= 0)
+                assert np.all(np.diff(d.astype(np.int64)) >= 0)          # delay-ordered row
                 m = tgt == t
-                order = np.nonzero(one["src"] == s)[0]
+                mine = np.nonzero(one["src"] == s)[0]
+                order = mine[np.argsort(one["d"][mine], kind="stable")]    # (delay, k) order
                 np.testing.assert_array_equal(d[m].astype(np.int64), one["d"][order])
                 assert f32_ulp_distance(w[m], one["w"][order].astype(np.float32)).max() <= 4
     ctx.destroy()

@@ -54,14 +54,14 @@ def test_dry_run_of_a_1024_rank_network():
     """Rank 5's share of a balanced network of 1,024 x 20,000 neurons (K = 400 + 100):
     exactly M x K synapses, built without the other 1,023 ranks' connections.  Its
     records carry generation positions (24 bits) where the network-wide counter would
-    need 34 bits beside a 25-bit key (10 rank-slot bits, 15 source bits)."""
+    need 34 bits beside a 31-bit key."""
     R = 1024
     net = wl.balanced(16000 * R, 4000 * R, 400, 100, wl.DELAY_NORMAL, seed=11, n_ranks=R)
     dry = gpu_build(net, dry_run_rank=5)
     s = dry.stats()
     M = sum(1 for _ in range(5, net.n_neurons, R))
     assert s["n_synapses"] == M * 500
-    assert s["key_bits"] == 25
+    assert s["key_bits"] == 31
     row = dry.get_row(5, 7)                      # local row 7: the outgoing synapses of gid 7 * R + 5
     c = dry.get_connections(5)
     assert c["row_ptr"][-1] == M * 500

@@ -66,8 +66,8 @@ def test_per_target_generation_equals_full():
 
 
 def test_partition_invariance_and_layout_order():
-    """Every partition flattens to the 1-rank multiset; a row holds one source's
-    connections in generation order (the stable sort by source)."""
+    """Every partition flattens to the 1-rank multiset; rows hold (source, delay)
+    sorted connections, ties in generation order."""
     net = wl.balanced(300, 75, 40, 10, wl.DELAY_NORMAL, seed=5)
     syn = oc.generate(net)
     ref = ol.flatten(ol.build_all(syn, ol.round_robin(net.n_neurons, 1))["ranks"],
@@ -84,7 +84,8 @@ def test_partition_invariance_and_layout_order():
             assert rp[-1] == len(rk["tgt"])
             for r in range(len(rp) - 1):
                 a, b = rp[r], rp[r + 1]
-                assert np.all(np.diff(rk["gidx"][a:b]) > 0)
+                key = rk["d"][a:b] * (1 << 40) + rk["gidx"][a:b]
+                assert np.all(np.diff(key) > 0)
                 assert np.all(rk["src"][a:b] == rk["src"][a])
 
 
