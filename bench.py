@@ -125,15 +125,15 @@ TRAFFIC = {
     # taken on step_update_kernel, the overlapped form with the same per-neuron loads and stores
     "update_kernel": {"bytes_per_unit": 15.71, "source": "sim.cu", "function": "step_update_kernel",
                       "function_sha": "9ea0313c697d5f62"},
+    # construction: the last capture of the (source, delay) layout (three 8/9-bit passes);
+    # the kernels changed since, so these read null until retaken
     "gen_kernel": {"bytes_per_unit": 7.99, "source": "build.cu", "function": "gen_kernel",
-                   "function_sha": "c509c81f4a7a4b1b"},
-    # the mean of the 9-bit (17.00) and the 10-bit (17.22) pass
-    "onesweep_pass": {"bytes_per_unit": 17.11, "source": "build.cu", "function": "onesweep_pass",
-                      "function_sha": "61cc3760491b97d0"},
-    "finalize_kernel": {"bytes_per_unit": 17.09, "source": "build.cu", "function": "finalize_kernel",
-                        "function_sha": "165501cd1dfda545"},
+                   "function_sha": "1c13fb751fed548c"},
+    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "function": "onesweep_pass",
+                      "function_sha": "cf4b5220d2dae599"},
+    "finalize_kernel": {"bytes_per_unit": 17.06, "source": "build.cu", "function": "finalize_kernel",
+                        "function_sha": "12d6e8b26fcfb879"},
 }
-
 
 def kernel_text_sha(path: str, function: str) -> str:
     """sha256[:16] of a kernel's definition: from its __global__ line to the closing brace
