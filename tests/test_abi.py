@@ -54,6 +54,23 @@ def test_struct_layouts_match_c():
     assert int(got[-1]) == _lib.snn_stats_t.sort_passes.offset
 
 
+def test_every_struct_field_offset_matches_c():
+    """Every field of every bound struct sits at the C compiler's offset (a field added
+    or reordered on one side only is caught even when the sizes agree)."""
+    names = ["snn_config", "snn_iaf_psc_exp_params", "snn_rule", "snn_dist", "snn_stats_t", "snn_allocator"]
+    fields = [(n, f[0]) for n in names for f in getattr(_lib, n)._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"snn.h\"\nint main(){" + "".join(
+        f'printf("%zu\\n", offsetof({n}, {f}));' for n, f in fields) + "return 0;}"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    want = [getattr(getattr(_lib, n), f).offset for n, f in fields]
+    assert got == want, [(nf, g, w) for nf, g, w in zip(fields, got, want) if g != w]
+
+
 def test_missing_library_fails_loudly(tmp_path):
     saved = _lib._lib
     try:

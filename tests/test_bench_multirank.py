@@ -1,5 +1,6 @@
-"""bench.py's multi-rank aggregation (N independent replicas, weak scaling) with two
-gloo ranks on the CPU: units add up, the time is the slowest rank's."""
+"""bench.py on the CPU: its multi-rank aggregation (N independent replicas, weak
+scaling) with two gloo ranks -- units add up, the time is the slowest rank's -- and its
+table of measured DRAM traffic per kernel."""
 import os
 import socket
 
@@ -49,3 +50,19 @@ def test_two_rank_aggregate():
 def test_single_process_aggregate_is_identity():
     import bench
     assert bench.aggregate(5.0, 2.0) == (5.0, 2.0)
+
+
+def test_traffic_table_names_existing_kernels():
+    """Every kernel of the bench's measured-traffic table exists in its source file, so a
+    figure can only read null because its kernel changed since the capture, never because
+    the name no longer resolves."""
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for name, d in bench.TRAFFIC.items():
+        src = os.path.join(root, "paper_2512_09502_gb300", "csrc", d["source"])
+        assert len(bench.kernel_text_sha(src, d["function"])) == 16, name
+        t = bench.traffic_of(name, 1.0)
+        assert t is None or t == d["bytes_per_unit"]
