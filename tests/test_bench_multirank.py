@@ -66,3 +66,24 @@ def test_traffic_table_names_existing_kernels():
         assert len(bench.kernel_text_sha(src, d["function"])) == 16, name
         t = bench.traffic_of(name, 1.0)
         assert t is None or t == d["bytes_per_unit"]
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` times the oracle on a bounded sample and prints one JSON
+    line carrying the contract's keys: the arm, the metric and unit of the GPU arm, a value,
+    a cpu_baseline describing the sample, and an e2e entry without host-device bytes."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--ref-neurons", "200", "--ref-sim-steps", "50"],
+                         capture_output=True, text=True, check=True, timeout=600, cwd=root).stdout
+    lines = [x for x in out.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "(synapses + events)/s" and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "200 neurons" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
