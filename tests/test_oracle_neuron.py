@@ -121,3 +121,63 @@ def test_poisson_drive_counts_distribution_and_independence():
     assert abs(r) < 4 / math.sqrt(counts[:-1].size)
     # a drive over a sub-range draws the same counts as over the whole range
     np.testing.assert_array_equal(on.poisson_counts(thr, 0, 1234, 1001, 57, 3), counts[3, 1001:1058])
+
+
+def _vinit_net(pops):
+    return wl.Network("vinit", [wl.Population(n, p) for n, p in pops], [], [])
+
+
+def test_initial_v_range_and_uniformity():
+    """V0 = lo + (hi - lo) u01(word) lies strictly inside (lo, hi) and is uniform there:
+    KS test against U(lo, hi) over 10^5 neurons, per population, with the two
+    populations' draws uncorrelated and consecutive neurons uncorrelated."""
+    from scipy import stats
+    pa = wl.NeuronParams(V_init_lo=-3.0, V_init_hi=19.5, v_init_seed=9)
+    pb = wl.NeuronParams(V_init_lo=2.0, V_init_hi=7.0, v_init_seed=9)
+    n = 100_000
+    v = on.initial_v(_vinit_net([(n, pa), (n, pb)]))
+    assert v.shape == (2 * n,)
+    for (lo, hi), part in (((-3.0, 19.5), v[:n]), ((2.0, 7.0), v[n:])):
+        assert part.min() > lo and part.max() < hi
+        assert stats.kstest(part, stats.uniform(loc=lo, scale=hi - lo).cdf).pvalue > 1e-3
+    ua = (v[:n] + 3.0) / 22.5
+    ub = (v[n:] - 2.0) / 5.0
+    lim = 4 / math.sqrt(n)
+    assert abs(np.corrcoef(ua, ub)[0, 1]) < lim          # same seed, other population
+    assert abs(np.corrcoef(ua[:-1], ua[1:])[0, 1]) < lim  # neighbours
+
+
+def test_initial_v_exact_at_word_extremes(monkeypatch):
+    """The exact V0 for VINIT words 0, 2^9 and 0xFFFFFFFF: u01 gives 2^-24, 3 * 2^-24 and
+    1 - 2^-24, so V0 = lo + (hi - lo) u exactly.  The three other words of the block are
+    set to other values, so the test also fixes which word is used; the recorded call
+    fixes the stream: counter = gid, word2 = population index, purpose VINIT, the
+    population's seed."""
+    from oracle import philox as ph
+    calls = []
+    words = np.array([0, 512, 0xFFFFFFFF], dtype=np.uint64)
+
+    def fake_stream(counter, word2, purpose, seed):
+        calls.append((np.array(counter), word2, purpose, seed))
+        other = np.full(len(counter), 0x80000000, dtype=np.uint64)
+        return words[:len(counter)], other, other, other
+
+    monkeypatch.setattr(on.ph, "stream", fake_stream)
+    lo, hi = 1.25, 17.75
+    p0 = wl.NeuronParams()                                   # lo == hi: no draw
+    p1 = wl.NeuronParams(V_init_lo=lo, V_init_hi=hi, v_init_seed=77)
+    v = on.initial_v(_vinit_net([(4, p0), (3, p1)]))
+    u = np.array([2.0 ** -24, 3 * 2.0 ** -24, 1 - 2.0 ** -24])
+    np.testing.assert_array_equal(v[:4], 0.0)
+    np.testing.assert_array_equal(v[4:], lo + (hi - lo) * u)
+    assert len(calls) == 1
+    ctr, word2, purpose, seed = calls[0]
+    np.testing.assert_array_equal(ctr, [4, 5, 6])
+    assert (word2, purpose, seed) == (1, ph.PURPOSE_VINIT, 77)
+
+
+def test_initial_v_constant_when_range_is_empty():
+    p = wl.NeuronParams(V_init_lo=5.0, V_init_hi=5.0, v_init_seed=1)
+    q = wl.NeuronParams(V_init_lo=5.0, V_init_hi=4.0, v_init_seed=1)
+    v = on.initial_v(_vinit_net([(10, p), (6, q)]))
+    np.testing.assert_array_equal(v, 5.0)
