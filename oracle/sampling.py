@@ -73,6 +73,8 @@ def quantised_normal_table(mean: float, sd: float, lo: float, dt: float):
     below lo lands on s_min.  The table stops at the first s whose threshold reaches
     2^32; a table that would exceed 255 steps is rejected (delays are stored in u8)."""
     s_min = max(1, int(round(lo / dt)))
+    if s_min > MAX_DELAY_STEPS:        # the clipped mass below lo lands on s_min itself
+        raise ValueError("delay distribution has mass above 255 steps")
     thr = []
     s = s_min
     while True:

@@ -230,8 +230,12 @@ int check_dist_d(const snn_dist* d) {
 int delay_table(double mean, double sd, double lo, double dt, uint32_t* s_min,
                 std::vector<uint32_t>* thr) {
   std::fesetround(FE_TONEAREST);
-  const int smin = std::max(1, (int)std::nearbyint(lo / dt));
   thr->clear();
+  // delays are stored in u8: the smallest step itself must fit before any threshold is
+  // looked at (the clipped mass below lo lands on it)
+  if (!(lo / dt < 255.5)) return SNN_EINVAL;
+  const int smin = std::max(1, (int)std::nearbyint(lo / dt));
+  if (smin > 255) return SNN_EINVAL;
   int s = smin;
   while (true) {
     const double x = ((s + 0.5) * dt - mean) / sd;
@@ -248,7 +252,8 @@ int delay_table(double mean, double sd, double lo, double dt, uint32_t* s_min,
 
 uint32_t const_delay_steps(double d, double dt) {
   std::fesetround(FE_TONEAREST);
-  return (uint32_t)std::max(1.0, std::nearbyint(d / dt));
+  // clamped below the u32 range before the conversion; callers reject anything above 255
+  return (uint32_t)std::min(65535.0, std::max(1.0, std::nearbyint(d / dt)));
 }
 
 // Integer CDF table of Poisson(rate * h / 1000).

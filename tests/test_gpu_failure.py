@@ -42,7 +42,7 @@ def test_failing_allocator_returns_enomem():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("bad", ["delay_above_255", "range", "after_calibrate"])
+@pytest.mark.parametrize("bad", ["delay_above_255", "clip_step_above_255", "range", "after_calibrate"])
 def test_invalid_arguments_rejected(bad):
     ensure_lib()
     ctx = _lib.Context()
@@ -50,6 +50,10 @@ def test_invalid_arguments_rejected(bad):
     rule = wl.Rule(wl.RULE_FIXED_INDEGREE, 3)
     if bad == "delay_above_255":
         pr = wl.Projection(0, 100, 0, 100, rule, wl.Dist(wl.W_CONST, 1.0), wl.Dist(wl.D_NORMAL_MIN, 25.0, 2.0, 0.1), 1)
+    elif bad == "clip_step_above_255":
+        # clipped below at 30 ms (300 steps) with the normal's mass far below: every delay
+        # would be the clip step, which a u8 delay cannot hold
+        pr = wl.Projection(0, 100, 0, 100, rule, wl.Dist(wl.W_CONST, 1.0), wl.Dist(wl.D_NORMAL_MIN, 1.5, 0.75, 30.0), 1)
     elif bad == "range":
         pr = wl.Projection(0, 101, 0, 100, rule, wl.Dist(wl.W_CONST, 1.0), wl.Dist(wl.D_CONST, 1.0), 1)
     else:

@@ -111,6 +111,23 @@ def test_quantised_normal_sample_chi_square():
 def test_delay_table_rejects_above_255():
     with pytest.raises(ValueError):
         sm.quantised_normal_table(25.0, 2.0, 0.1, 0.1)
+    # clipped below at 30 ms = 300 steps with the normal's mass far below it: every
+    # delay would be the clip step itself, which does not fit a u8
+    with pytest.raises(ValueError):
+        sm.quantised_normal_table(1.5, 0.75, 30.0, 0.1)
+
+
+def test_delay_table_clip_step_at_255_is_kept():
+    """lo = 25.5 ms at dt = 0.1 ms: the clip step is 255, the largest u8 delay, and all
+    the normal's mass lies below it, so the table is empty and every delay is 255."""
+    s_min, thr = sm.quantised_normal_table(1.5, 0.75, 25.5, 0.1)
+    assert s_min == 255 and len(thr) == 0
+    assert sm.max_delay_steps(wl_dist_normal(1.5, 0.75, 25.5), 0.1) == 255
+
+
+def wl_dist_normal(mean, sd, lo):
+    from paper_2512_09502_gb300 import workloads as wl
+    return wl.Dist(wl.D_NORMAL_MIN, mean, sd, lo)
 
 
 def test_poisson_table_matches_scipy():
