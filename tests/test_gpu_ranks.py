@@ -1,5 +1,7 @@
 """Logical ranks on one GPU: per-rank layouts, image neurons and every communication
 map against the oracle's per-rank construction, through the C ABI."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -33,31 +35,41 @@ def test_rank_layouts_and_maps_match_oracle(R):
 
 
 @pytest.mark.parametrize("exchange", ["p2p", "collective"])
-def test_rank_simulation_matches_oracle(exchange):
-    """Spikes routed through the maps reach the same targets: V after 100 steps
-    within 1e-4 mV of the single-rank oracle, and the early spike trains equal."""
-    R = 5
-    net = _net(R, seed=11)
+@pytest.mark.parametrize("j_scale", [0.1, 1.0])
+def test_rank_simulation_matches_oracle(exchange, j_scale):
+    """Spikes routed through the maps reach the same targets as in the single-rank
+    FP64 oracle: V after every one of 100 steps within 1e-4 mV of the oracle's.  With
+    recurrent weights at 1/10 (no chaotic amplification) the spike trains must be equal
+    over all 100 steps; at full strength a threshold decision taken in the two
+    precisions may flip, and V is compared at every step before the first step whose
+    spikes differ, which must come after spikes have been delivered."""
+    R, steps = 5, 100
+    prm = dataclasses.replace(wl.BALANCED_PARAMS, V_init_lo=0.0, V_init_hi=19.9, v_init_seed=5)
+    net = wl.balanced(240, 61, 30, 8, wl.DELAY_NORMAL, seed=11, n_ranks=R, j_scale=j_scale, params=prm)
     net.drives = [wl.Drive(0, net.n_neurons, 16000.0, wl.J_E, 4)]
     ctx = gpu_build(net, exchange=exchange, spike_log_capacity=1 << 20, use_graph=False)
     syn, ref = oracle_layout(net, R=1)
     rk = ref["ranks"][0]
     sim = on.Simulator(net, rk["row_ptr"], rk["tgt"], rk["d"], rk["w"].astype(np.float32).astype(np.float64),
                        on.ring_slots_for(oc.max_delay(net)))
-    spikes, _ = sim.run(100)
-    ctx.simulate(100)
-    V, _, _ = ctx.get_state(0, net.n_neurons)
+    vg, vo, so = [], [], []
+    for _ in range(steps):
+        ctx.simulate(1)
+        vg.append(ctx.get_state(0, net.n_neurons)[0])
+        so.append(sorted(sim.step().tolist()))
+        vo.append(sim.V.copy())
     st, gid = ctx.get_spikes()
-    o = sorted(spikes)
-    g = sorted(zip(st.tolist(), gid.tolist()))
-    assert len(o) > 0
-    if o == g:
-        assert np.max(np.abs(V - sim.V)) <= 1e-4
-    else:
-        # a threshold decision taken in different precisions may flip; everything
-        # before the first flip must agree exactly
-        first = next(k for k in range(min(len(o), len(g))) if o[k] != g[k]) if len(o) and len(g) else 0
-        assert first > 0
+    sg = [[] for _ in range(steps)]
+    for s, g in zip(st.tolist(), gid.tolist()):
+        sg[s].append(g)
+    sg = [sorted(x) for x in sg]
+    first_diff = next((n for n in range(steps) if so[n] != sg[n]), steps)
+    if j_scale < 1.0:
+        assert first_diff == steps
+    first_spike = next(n for n in range(steps) if so[n])
+    assert first_diff >= first_spike + 3       # delivered input has entered V before the compare ends
+    for n in range(first_diff):
+        assert np.max(np.abs(vg[n] - vo[n])) <= 1e-4, n
     ctx.destroy()
 
 
