@@ -11,6 +11,7 @@
 // digit histograms) taken from one file-scope __device__ scratch array of fixed size.
 // The caller passes only its input description and its output buffers.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -102,10 +103,18 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
     std::snprintf(msg, mlen, __VA_ARGS__);      \
     return code;                                \
   } while (0)
-#define NA_CK(call)                                                                   \
-  do {                                                                                \
-    const cudaError_t e__ = (call);                                                   \
-    if (e__ != cudaSuccess) NA_FAIL(SNN_ECUDA, "%s: %s", #call, cudaGetErrorString(e__)); \
+  // Once work is queued on the stream, a failing call first waits for that work: the
+  // queued kernels use the shared scratch, and the next call (perhaps on another
+  // stream) would otherwise clear it under them.
+  bool enqueued = false;
+#define NA_CK(call)                                                      \
+  do {                                                                   \
+    const cudaError_t e__ = (call);                                      \
+    if (e__ != cudaSuccess) {                                            \
+      if (enqueued) (void)cudaStreamSynchronize(st);                     \
+      NA_FAIL(SNN_ECUDA, "%s: %s", #call, cudaGetErrorString(e__));      \
+    }                                                                    \
+    enqueued = true;                                                     \
   } while (0)
 
   if (!rule || !weight || !delay || !dev_row_ptr || !(dt_ms > 0) || n_neurons == 0 || n_src == 0 ||
@@ -114,14 +123,15 @@ extern "C" int snn_connect_sorted_noalloc(uint32_t n_neurons, uint32_t src_first
   if ((uint64_t)src_first + n_src > n_neurons || (uint64_t)tgt_first + n_tgt > n_neurons)
     NA_FAIL(SNN_EINVAL, "projection range beyond n_neurons");
   uint64_t E = 0;
-  if (rule->kind == SNN_RULE_FIXED_INDEGREE) {
-    if (!(rule->param >= 1) || rule->param != (double)(uint64_t)rule->param)
-      NA_FAIL(SNN_EINVAL, "fixed in-degree needs an integer K >= 1");
-    E = (uint64_t)rule->param * n_tgt;
-  } else if (rule->kind == SNN_RULE_FIXED_TOTAL) {
-    if (!(rule->param >= 1) || rule->param != (double)(uint64_t)rule->param)
-      NA_FAIL(SNN_EINVAL, "fixed total number needs an integer N >= 1");
-    E = (uint64_t)rule->param;
+  if (rule->kind == SNN_RULE_FIXED_INDEGREE || rule->kind == SNN_RULE_FIXED_TOTAL) {
+    if (!(rule->param >= 1) || rule->param != std::floor(rule->param))
+      NA_FAIL(SNN_EINVAL, "%s needs an integer parameter >= 1",
+              rule->kind == SNN_RULE_FIXED_INDEGREE ? "fixed in-degree" : "fixed total number");
+    // bounded before the integer conversion and the product, so that neither wraps
+    const uint64_t per_tgt_cap = rule->kind == SNN_RULE_FIXED_INDEGREE ? kMaxSynapses / n_tgt : kMaxSynapses;
+    if (rule->param > (double)per_tgt_cap)
+      NA_FAIL(SNN_EINVAL, "more synapses than the allocation-free limit of %llu", (unsigned long long)kMaxSynapses);
+    E = rule->kind == SNN_RULE_FIXED_INDEGREE ? (uint64_t)rule->param * n_tgt : (uint64_t)rule->param;
   } else {
     NA_FAIL(SNN_EINVAL, "only fixed in-degree and fixed total number are supported here");
   }

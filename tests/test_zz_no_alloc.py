@@ -17,10 +17,19 @@ from paper_2512_09502_gb300 import _lib, workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-def _projection():
+def _projection(kind):
+    """One projection of each shape the entry point builds: fixed in-degree with normal
+    delays, fixed total number (the draw-indexed generation branch) and a constant
+    delay (the branch without a delay table)."""
     p = wl.BALANCED_PARAMS
-    pr = wl.Projection(0, 2500, 0, 3000, wl.Rule(wl.RULE_FIXED_INDEGREE, 50),
-                       wl.Dist(wl.W_NORMAL_SIGN, 87.8, 8.78), wl.DELAY_NORMAL, 1234)
+    w = wl.Dist(wl.W_NORMAL_SIGN, 87.8, 8.78)
+    if kind == "fixed_indegree":
+        pr = wl.Projection(0, 2500, 0, 3000, wl.Rule(wl.RULE_FIXED_INDEGREE, 50), w, wl.DELAY_NORMAL, 1234)
+    elif kind == "fixed_total":
+        pr = wl.Projection(500, 2000, 0, 3000, wl.Rule(wl.RULE_FIXED_TOTAL, 150_000), w, wl.DELAY_NORMAL, 77)
+    else:
+        pr = wl.Projection(0, 3000, 1000, 1700, wl.Rule(wl.RULE_FIXED_INDEGREE, 40), w,
+                           wl.Dist(wl.D_CONST, 1.5), 9)
     net = wl.Network("noalloc", [wl.Population(3000, p)], [pr], [])
     return net, pr
 
@@ -43,10 +52,11 @@ def _call(lib, torch, n_neurons, pr, cap, stream):
     return rc, n.value, msg.value.decode(), rp, tgt, w, d
 
 
-def test_noalloc_matches_calibrate_twice():
+@pytest.mark.parametrize("kind", ["fixed_indegree", "fixed_total", "const_delay"])
+def test_noalloc_matches_calibrate_twice(kind):
     torch = pytest.importorskip("torch")
     lib = ensure_lib()
-    net, pr = _projection()
+    net, pr = _projection(kind)
     ref_ctx = gpu_build(net)
     ref = ref_ctx.get_connections(0)
     ref_ctx.destroy()
