@@ -110,7 +110,11 @@ typedef struct snn_config {
                                   as the key needs); 0 = 10                             */
   int32_t device;              /* CUDA device ordinal                                  */
   int32_t profile_kernels;     /* time every update / deliver launch with CUDA events
-                                  (no graph then); results in snn_stats_t              */
+                                  (no graph then); results in snn_stats_t.  1: on the
+                                  schedule the steps run (one rank: the neuron work and
+                                  the delivery of a step overlap on two streams, each
+                                  timed on its own stream); 2: the sequential update ->
+                                  deliver chain, also on one rank                      */
   int32_t sort_items;          /* records per thread of a sort tile: 8, 12, 16; 0 = tuned */
   int32_t deliver_ctas_per_sm; /* delivery grid = SMs x this (1..32); 0 = tuned          */
   /* Dry run (Results, "Collective communication": each process builds its regular share

@@ -165,7 +165,7 @@ class Context:
     def __init__(self, *, dt: float = 0.1, n_ranks: int = 1, weight_format: str = "f32",
                  exchange: str = "p2p", use_graph: bool = True, spike_log_capacity: int = 0,
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
-                 stream: Optional[int] = None, profile_kernels: bool = False, sort_items: int = 0,
+                 stream: Optional[int] = None, profile_kernels: int = 0, sort_items: int = 0,
                  deliver_ctas_per_sm: int = 0, dry_run_rank: Optional[int] = None, xi: float = 0.0):
         self.lib = load()
         if not (radix_bits and sort_items and deliver_ctas_per_sm):
@@ -176,7 +176,7 @@ class Context:
             deliver_ctas_per_sm = deliver_ctas_per_sm or int(tuned.get("deliver_ctas_per_sm", 0))
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
-                         1 if profile_kernels else 0, sort_items, deliver_ctas_per_sm,
+                         int(profile_kernels), sort_items, deliver_ctas_per_sm,
                          0 if dry_run_rank is None else 1, 0 if dry_run_rank is None else dry_run_rank,
                          float(xi))
         self._allocator = allocator

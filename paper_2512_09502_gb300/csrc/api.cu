@@ -355,6 +355,7 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
                                  config->dry_run_rank >= config->n_ranks))
       return SNN_EINVAL;
     if (!(config->xi == config->xi)) return SNN_EINVAL;    // NaN threshold
+    if (config->profile_kernels < 0 || config->profile_kernels > 2) return SNN_EINVAL;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
@@ -827,6 +828,7 @@ int snn_calibrate(snn_ctx* c) {
   if (!dry) {
   SimArgs& s = c->sim;
   s.N = N; s.R = R;
+  s.err = c->d_err;
   AL(s.V, N, "V"); AL(s.Iex, N, "Iex"); AL(s.Iin, N, "Iin"); AL(s.refr, N, "refr");
   std::vector<uint16_t> pop_of(N);
   std::vector<DevPop> dpops;
@@ -960,7 +962,7 @@ int snn_calibrate(snn_ctx* c) {
 // ---------------------------------------------------------------------------
 // Kernels one batch of `steps` steps launches.
 static uint64_t launches_per_batch(snn_ctx* c, uint32_t steps) {
-  if (c->overlap && !c->cfg.profile_kernels) return 2ull * steps + 2;
+  if (c->overlap && c->cfg.profile_kernels != 2) return 2ull * steps + 2;
   return (uint64_t)steps * (2 + (c->cfg.n_ranks > 1 ? route_kernels_per_step(c) : 0)) + 1;
 }
 
@@ -968,21 +970,51 @@ static uint64_t launches_per_batch(snn_ctx* c, uint32_t steps) {
 // per step k the delivery of step k (stream st2, after the neuron work that listed its
 // spikes) runs beside step_update(k) (stream st, after the delivery of step k - 1,
 // whose slots it reads).  The last step_update takes the input only.
+// With profile_kernels the same schedule runs (no graph) with a pair of timing events
+// around every launch on its own stream, so each kernel is timed beside the other one as
+// in the graph-captured steps.
 static int run_steps_overlapped(snn_ctx* c, uint32_t steps) {
   SimArgs& o = c->ov;
   cudaStream_t A = c->st, B = c->st2;
+  const bool profile = c->cfg.profile_kernels && !c->capturing;
+  std::vector<cudaEvent_t> evs;
+  if (profile) {
+    evs.resize(4 * (size_t)steps + 2);
+    for (auto& e : evs) CK(cudaEventCreate(&e));
+  }
+  if (profile) CK(cudaEventRecord(evs[4 * (size_t)steps], A));
   CK(launch_step_update(o, 0, kStepPre, A));
+  if (profile) CK(cudaEventRecord(evs[4 * (size_t)steps + 1], A));
   CK(cudaEventRecord(c->ev_u, A));
   for (uint32_t k = 0; k < steps; ++k) {
     if (k > 0) CK(cudaStreamWaitEvent(A, c->ev_d, 0));
     CK(cudaStreamWaitEvent(B, c->ev_u, 0));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k], B));
     CK(launch_deliver(o, k, B, false));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 1], B));
     CK(cudaEventRecord(c->ev_d, B));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 2], A));
     CK(launch_step_update(o, k, kStepPost | (k + 1 < steps ? kStepPre : 0u), A));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 3], A));
     CK(cudaEventRecord(c->ev_u, A));
   }
   CK(cudaStreamWaitEvent(A, c->ev_d, 0));
   CK(launch_advance(o, steps, A));
+  if (profile) {
+    CK(cudaStreamSynchronize(A));
+    float u = 0, d = 0;
+    CK(cudaEventElapsedTime(&u, evs[4 * (size_t)steps], evs[4 * (size_t)steps + 1]));
+    c->stats.t_update_ms += u;
+    for (uint32_t k = 0; k < steps; ++k) {
+      CK(cudaEventElapsedTime(&d, evs[4 * (size_t)k], evs[4 * (size_t)k + 1]));
+      c->stats.t_deliver_ms += d;
+      CK(cudaEventElapsedTime(&u, evs[4 * (size_t)k + 2], evs[4 * (size_t)k + 3]));
+      c->stats.t_update_ms += u;
+    }
+    for (auto& e : evs) cudaEventDestroy(e);
+    c->stats.update_launches += steps + 1;
+    c->stats.deliver_launches += steps;
+  }
   if (!c->capturing) c->stats.kernel_launches += launches_per_batch(c, steps);
   return SNN_OK;
 }
@@ -990,7 +1022,7 @@ static int run_steps_overlapped(snn_ctx* c, uint32_t steps) {
 static int run_steps(snn_ctx* c, uint32_t steps) {
   SimArgs& s = c->sim;
   if (steps == 0) return SNN_OK;
-  if (c->overlap && !c->cfg.profile_kernels) return run_steps_overlapped(c, steps);
+  if (c->overlap && c->cfg.profile_kernels != 2) return run_steps_overlapped(c, steps);
   const bool routed = c->cfg.n_ranks > 1;
   const bool profile = c->cfg.profile_kernels && !c->capturing;
   std::vector<cudaEvent_t> evs;

@@ -546,10 +546,14 @@ __device__ __forceinline__ void deliver_span(const SimArgs& a, const WT* __restr
 #pragma unroll
     for (int k = 0; k < DEL_ILP; ++k) {
       const uint64_t e = e0 + (uint64_t)k * st;
-      if (e < hi && tt[k] < a.N) {
-        const uint32_t slot = (n + dd[k]) & a.ring_mask;
-        const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
-        red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
+      if (e < hi) {
+        if (tt[k] < a.N) {
+          const uint32_t slot = (n + dd[k]) & a.ring_mask;
+          const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
+          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
+        } else {
+          atomicOr(a.err, kErrBounds);    // corrupt connection: flagged, never written
+        }
       }
     }
   }

@@ -31,6 +31,7 @@ struct SimArgs {
   uint32_t slices;                            // slices of one row (several CTAs per row)
   uint32_t deliver_grid, update_grid;
   uint32_t lists;                             // spike / work lists cycled: 2, or 3 (overlapped steps)
+  uint32_t* err;                              // device error word (kErrBounds: an event's target out of range)
 };
 
 // Overlapped steps (one rank): the neuron work of step k and the delivery of step k run

@@ -90,12 +90,12 @@ def test_graph_and_stream_paths_agree():
 def test_overlapped_steps_match_the_sequential_schedule():
     """One rank runs the neuron work of step k beside the delivery of step k (two
     streams, spikes of step k + 1 decided one step ahead).  Against the sequential
-    update -> deliver chain (profile_kernels): the same early spikes, and after
+    update -> deliver chain (profile_kernels = 2): the same early spikes, and after
     simulate(T) nothing of step T is visible -- no logged spike at step >= T, the same
     state within rounding as the sequential run after T steps."""
     p = wl.NeuronParams(V_init_lo=0.0, V_init_hi=19.9, v_init_seed=5)
     net = wl.balanced(1001, 250, 37, 9, wl.DELAY_NORMAL, seed=3, params=p, drive_rate_hz=20000.0)
-    seq = gpu_build(net, spike_log_capacity=1 << 20, use_graph=False, profile_kernels=True)
+    seq = gpu_build(net, spike_log_capacity=1 << 20, use_graph=False, profile_kernels=2)
     ovl = gpu_build(net, spike_log_capacity=1 << 20, use_graph=False)
     for T in (1, 2, 5, 12, 20):      # 40 steps in calls of several lengths
         seq.simulate(T)
