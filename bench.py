@@ -41,11 +41,22 @@ BYTES = {"sort_pass": 16.0, "deliver_f32": 13.0, "deliver_bf16": 11.0, "finalize
 
 
 WORKLOADS = ("balanced_500k", "balanced_5k", "multi_area", "multi_area_r128", "indegree_x2", "indegree_x5",
-             "indegree_x10")
+             "indegree_x10", "update_500k", "construction_112m", "deliver_500k")
 
 
 def workload(name: str, scale: float):
     from paper_2512_09502_gb300 import workloads as wl
+    # small cases for kernel profiles (a few GB on the device at most, larger than L2)
+    if name == "update_500k":           # the full-size neuron update on a layout of a few hundred MB
+        p = wl.NeuronParams(V_init_lo=0.0, V_init_hi=19.9, v_init_seed=5)
+        return wl.balanced(400000, 100000, 8, 2, wl.DELAY_NORMAL, seed=7, params=p, drive_rate_hz=20000.0,
+                           name="update_500k")
+    if name == "construction_112m":     # 112.5M synapses, the 500k network's 19-bit source key
+        return wl.balanced(240000, 60000, 300, 75, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0,
+                           name="construction_112m")
+    if name == "deliver_500k":          # the full-size 128 MB ring, 450M synapses, input K x J as at full size
+        return wl.balanced(400000, 100000, 720, 180, wl.DELAY_NORMAL, seed=7, drive_rate_hz=20000.0,
+                           j_scale=12.5, name="deliver_500k")
     if name == "balanced_500k":
         return wl.balanced_scaled(scale)
     if name == "balanced_5k":
@@ -117,8 +128,7 @@ class Clocks:
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of full-size one-pass
 # ncu captures of the timed step, divided by the units the launches processed), with the
 # kernel whose source text was measured (file, function, sha256[:16] of the function's
-# text at capture time); profiles/traffic_balanced_500k.md gives the commands and the
-# raw figures.
+# text at capture time).
 TRAFFIC = {
     "deliver_kernel": {"bytes_per_unit": 23.24, "source": "sim.cu", "function": "deliver_kernel",
                        "function_sha": "b3ca0bf24329b8ff"},
@@ -160,14 +170,15 @@ def traffic_of(kernel: str, units_per_launch: float):
     return d["bytes_per_unit"] * units_per_launch
 
 
-def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000):
+def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000, name: str = "balanced_500k"):
     """The oracle on a bounded sample of the workload: the same balanced network
     (same in-degrees, weights, delays, drive, hence the same dynamical regime) at
-    ``n_neurons`` neurons, built and then simulated for ``sim_steps`` steps."""
+    ``n_neurons`` neurons, built and then simulated for ``sim_steps`` steps; or, with
+    ``name="balanced_5k"``, the whole 5,000-neuron balanced network."""
     import numpy as np
     from oracle import connect as oc, layout as ol, neuron as on
     from paper_2512_09502_gb300 import workloads as wl
-    net = wl.balanced_scaled(scale * n_neurons / 500_000)
+    net = wl.balanced_small() if name == "balanced_5k" else wl.balanced_scaled(scale * n_neurons / 500_000)
     t0 = time.perf_counter()
     syn = oc.generate(net)
     rk = ol.build_rank(syn, ol.round_robin(net.n_neurons, 1), 0)
@@ -178,10 +189,69 @@ def cpu_sample(scale: float, n_neurons: int = 1000, sim_steps: int = 1000):
     events = int(np.sum(rk["row_ptr"][g + 1] - rk["row_ptr"][g])) if len(g) else 0
     dt = time.perf_counter() - t0
     units = len(syn["src"]) + events
+    what = ("the whole 5,000-neuron balanced network" if name == "balanced_5k" else
+            f"balanced network with the workload's in-degrees, weights, delays and drive at {net.n_neurons} neurons")
     return units / dt, dict(synapses=len(syn["src"]), events=events, seconds=dt,
-                            sample=f"balanced network with the workload's in-degrees, weights, delays and "
-                                   f"drive at {net.n_neurons} neurons ({len(syn['src'])} synapses), built "
-                                   f"then simulated {sim_steps} steps ({events} events)")
+                            sample=f"{what} ({len(syn['src'])} synapses), built then simulated {sim_steps} steps "
+                                   f"({events} events)")
+
+
+def _cpu_worker(job):
+    """One replica of the sample in a worker process (top level, so that spawned
+    workers can import it); job = (scale, n_neurons, sim_steps), or None to import the
+    oracle and return (pool warm-up)."""
+    if job is None:
+        import oracle.layout  # noqa: F401
+        import oracle.neuron  # noqa: F401
+        return None
+    return cpu_sample(*job)[1]
+
+
+class CpuPool:
+    """Worker processes for the oracle on every host core, started with ``spawn`` (a
+    forked child of a process that uses CUDA would hang) and warmed up before any timed
+    round."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+        self.pool.map(_cpu_worker, [None] * workers)
+
+    def round(self, scale: float, n_neurons: int, sim_steps: int):
+        """One replica of the sample per worker at once: whole-round units per second
+        of wall time, and the sample's description."""
+        t0 = time.perf_counter()
+        infos = self.pool.map(_cpu_worker, [(scale, n_neurons, sim_steps)] * self.workers)
+        dt = time.perf_counter() - t0
+        units = sum(i["synapses"] + i["events"] for i in infos)
+        return units, dt, infos[0]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_workers():
+    return max(1, min(cpu_cores() or 1, 16))
+
+
+def cpu_baseline(args):
+    """The oracle timed on the host cores: one replica of the bounded sample on one core,
+    then one replica per core at once (the sample is independent work, so the all-cores
+    figure is the replicas' summed units over the wall time of the round), and the whole
+    5,000-neuron balanced network on one core."""
+    v1, info = cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
+    v5k, info5k = cpu_sample(1.0, sim_steps=1000, name="balanced_5k")
+    pool = CpuPool(cpu_workers())
+    units, dt, _ = pool.round(args.scale, args.ref_neurons, args.ref_sim_steps)
+    pool.close()
+    full = 5.625e9 / info["synapses"] * info["seconds"]          # construction share scales with synapses
+    return {"value": units / dt, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": f"{pool.workers} concurrent replicas (one per core) of: {info['sample']}",
+            "serial": {"value": v1, "cores": 1, "seconds": info["seconds"]},
+            "balanced_5k_full": {"value": v5k, "cores": 1, "seconds": info5k["seconds"], "sample": info5k["sample"]},
+            "full_size_serial_s_extrapolated": full}
 
 
 def aggregate(units: float, ms: float, dist=None, device: str = "cpu"):
@@ -209,22 +279,24 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    pool = CpuPool(cpu_workers())
+    info = None
     for _ in range(args.warmup):
-        cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
-    vals, info = [], None
+        pool.round(args.scale, args.ref_neurons, args.ref_sim_steps)
     t0 = time.perf_counter()
     units = 0.0
     for _ in range(args.steps):
-        v, info = cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
-        units += info["synapses"] + info["events"]
-        vals.append(v)
+        u, _, info = pool.round(args.scale, args.ref_neurons, args.ref_sim_steps)
+        units += u
     dt = time.perf_counter() - t0
+    pool.close()
     value = units / dt
+    sample = f"{pool.workers} concurrent replicas (one per core) of: {info['sample']}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "sample": info["sample"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]},
+            "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -254,10 +326,14 @@ def run_ours(args):
         tuned = autotune.tune(net, allocator=alloc, stream=stream.cuda_stream, device=local,
                               sim_steps=min(args.sim_steps, 1000))
     knobs = {k: int(tuned[k]) for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm")} if tuned else {}
+    for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm"):
+        if getattr(args, k):
+            knobs[k] = getattr(args, k)
+    extra = {"xi": args.xi} if args.xi else {}
 
     def one(fmt, sim_steps, profile=False):
         ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
-                                 device=local, use_graph=True, profile_kernels=profile, **knobs)
+                                 device=local, use_graph=True, profile_kernels=profile, **knobs, **extra)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ctx.calibrate()
@@ -317,7 +393,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t = time.perf_counter()
         ctx = _lib.build_network(net, weight_format="f32", allocator=alloc, stream=stream.cuda_stream,
-                                 device=local, use_graph=True, **knobs)
+                                 device=local, use_graph=True, **knobs, **extra)
         ctx.calibrate()
         ctx.simulate(args.sim_steps)
         st = ctx.stats()
@@ -368,8 +444,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, info = cpu_sample(args.scale, args.ref_neurons, args.ref_sim_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]}
+        cpu = cpu_baseline(args)
 
     if rank == 0:
         line = {
@@ -383,8 +458,10 @@ def run_ours(args):
             "components": {"synapses_built_per_s": syn_per_s, "synaptic_events_per_s": ev_per_s,
                            "construct_ms": s0["t_calibrate_ms"], "simulate_ms": s0["t_simulate_ms"],
                            "generate_ms": s0["t_generate_ms"], "sort_ms": s0["t_sort_ms"],
-                           "finalize_ms": s0["t_finalize_ms"], "events_per_step": s0["n_events"] / args.sim_steps,
-                           "rate_hz": s0["n_spikes"] / net.n_neurons / (args.sim_steps * net.dt / 1000.0),
+                           "finalize_ms": s0["t_finalize_ms"], "events_per_step": s0["n_events"] / max(args.sim_steps, 1),
+                           "rate_hz": s0["n_spikes"] / net.n_neurons / (args.sim_steps * net.dt / 1000.0)
+                           if args.sim_steps else 0.0,
+                           "maps_ms": s0["t_maps_ms"], "n_images": s0["n_images"], "xi": args.xi,
                            "peak_device_GB": s0["peak_device_bytes"] / 1e9},
             "bf16": bf,
             "tuned": knobs,
@@ -415,6 +492,11 @@ def main():
     ap.add_argument("--ref-sim-steps", type=int, default=1000)
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    # launch parameters (override the tuner) and the all-sources image threshold
+    ap.add_argument("--radix-bits", dest="radix_bits", type=int, default=0)
+    ap.add_argument("--sort-items", dest="sort_items", type=int, default=0)
+    ap.add_argument("--deliver-ctas", dest="deliver_ctas_per_sm", type=int, default=0)
+    ap.add_argument("--xi", type=float, default=0.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
