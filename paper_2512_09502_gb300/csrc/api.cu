@@ -821,8 +821,8 @@ int snn_calibrate(snn_ctx* c) {
   CK(cudaEventRecord(ev[4], c->st));
 
   // ---- simulation state (a dry run builds connections only) ----
-  uint32_t D = 1;
-  while (D < dmax + 1) D <<= 1;
+  // ring slots: delays 1 .. dmax ahead of the slot being read, so dmax + 1 slots
+  const uint32_t D = dmax + 1;
   c->ring_slots = D;
   float* d_v0 = nullptr;
   if (!dry) {
@@ -882,7 +882,7 @@ int snn_calibrate(snn_ctx* c) {
   s.ring_stride = (N + 3u) & ~3u;
   AL(s.ring, (uint64_t)D * s.n_rec * s.ring_stride, "ring buffers");
   CK(cudaMemsetAsync(s.ring, 0, (size_t)D * s.n_rec * s.ring_stride * 4, c->st));
-  s.ring_mask = D - 1;
+  s.ring_slots = D;
   AL(s.step, 1, "step");
   AL(s.n_spk, 2, "spike counts");
   AL(s.spk, (uint64_t)2 * N, "spike lists");

@@ -54,6 +54,88 @@ __device__ __forceinline__ uint32_t guided_count(const uint32_t* thr, uint32_t l
   return c;
 }
 
+// Generation modes of a block: fixed in-degree with a random source (word x of the
+// synapse's Philox block), all-to-all (source = k), one-to-one (source = the target's
+// index), and fixed total number on one rank (draw index = counter, random source).
+constexpr int GenRandom = 0, GenAll = 1, GenOneToOne = 2, GenFixedTotal = 3;
+
+// The items of one generation tile: records e0 .. e0 + n - 1 of block blk.  ONE32: one
+// rank, counters as record ids and a key of at most 32 bits with its digit histograms
+// fused (the common case): no source-rank slot, 32-bit digit extraction.
+struct DigitPlan {
+  uint32_t sh[MAX_PASSES], mk[MAX_PASSES];   // digit p = (key >> sh[p]) & mk[p]; mk = 0: no pass
+};
+
+template <int MODE, bool DTAB, bool ONE32>
+__device__ __forceinline__ void gen_items(const BuildArgs& a, const DevBlock& blk, const DevProj& P,
+                                          const uint32_t* s_tbl, const uint8_t* s_guide,
+                                          uint32_t (*s_hist)[kHistStride], uint64_t e0, uint32_t n,
+                                          const DigitPlan& dp, bool fuse_hist) {
+  const Geom g = a.g;
+  const int tid = threadIdx.x;
+  const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
+  const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+  constexpr bool FI = MODE != GenFixedTotal;
+  // fixed in-degree: (target m, k) of this thread's first item, then incremental
+  uint64_t m = 0;
+  uint32_t k = 0;
+  if (FI) {
+    const uint64_t e = e0 + tid;
+    m = div_magic(e, P.K, P.magic_div);
+    k = (uint32_t)(e - m * P.K);
+  }
+  const uint64_t cstep = (uint64_t)blk.tstep * P.K;
+  uint64_t cm = ((uint64_t)blk.ti0 + m * blk.tstep) * P.K;   // counter of (target m, k = 0)
+  const uint32_t Kk = (uint32_t)P.K;
+  const uint64_t obase = blk.out_base;
+  const uint64_t cbase = P.cbase;
+  for (uint32_t i = tid; i < n; i += GEN_BLOCK) {
+    const uint64_t e = e0 + i;
+    const uint64_t c = FI ? cm + k : e;
+    const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id, kPurposeSynapse), key);
+    const uint32_t si = MODE == GenAll ? k : (MODE == GenOneToOne ? (uint32_t)c : uniform_index(b.x, P.n_src));
+    const uint32_t src = P.src_first + si * P.src_stride;
+    uint32_t d = P.d_const;
+    if (DTAB) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
+    if (ONE32) {
+      const uint32_t k32 = (src << g.db) | d;
+      a.rec_a[obase + e] = ((uint64_t)k32 << g.cbits) | ((cbase + c) & cmask);
+#pragma unroll
+      for (int p = 0; p < MAX_PASSES; ++p)
+        if (dp.mk[p]) atomicAdd(&s_hist[p][(k32 >> dp.sh[p]) & dp.mk[p]], 1u);
+    } else {
+      uint32_t sig = 0, s = src;
+      if (g.R > 1) {
+        s = (uint32_t)div_magic(src, g.R, g.magic_R);
+        sig = src - s * g.R;
+      }
+      const uint32_t slot = sig == blk.rank ? 0u : (sig < blk.rank ? sig + 1 : sig);
+      const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
+      const uint64_t cid = a.pos_counters ? obase + e : cbase + c;
+      a.rec_a[obase + e] = (kk << g.cbits) | (cid & cmask);
+      if (fuse_hist) {
+        if (g.key_bits <= 32) {
+          const uint32_t k32 = (uint32_t)kk;
+#pragma unroll
+          for (int p = 0; p < MAX_PASSES; ++p)
+            if (dp.mk[p]) atomicAdd(&s_hist[p][(k32 >> dp.sh[p]) & dp.mk[p]], 1u);
+        } else {
+#pragma unroll
+          for (int p = 0; p < MAX_PASSES; ++p)
+            if (dp.mk[p]) atomicAdd(&s_hist[p][(uint32_t)(kk >> dp.sh[p]) & dp.mk[p]], 1u);
+        }
+      }
+    }
+    if (FI) {                     // advance to item i + GEN_BLOCK
+      k += GEN_BLOCK;
+      while (k >= Kk) {
+        k -= Kk;
+        cm += cstep;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   constexpr int BINS = kHistStride;
   __shared__ uint32_t s_hist[MAX_PASSES][BINS];
@@ -65,12 +147,12 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   const Geom g = a.g;
   const uint32_t passes = a.passes;
   for (int i = tid; i < MAX_PASSES * BINS; i += GEN_BLOCK) (&s_hist[0][0])[i] = 0;
-  // per-pass digit extraction on the 32-bit key (key_bits <= 32 on this path)
-  uint32_t dsh[MAX_PASSES], dmk[MAX_PASSES];
+  // per-pass digit extraction of the sort key
+  DigitPlan dp;
 #pragma unroll
   for (int p = 0; p < MAX_PASSES; ++p) {
-    dsh[p] = a.pass_shift[p];
-    dmk[p] = p < (int)passes ? (1u << a.pass_bits[p]) - 1 : 0u;
+    dp.sh[p] = a.pass_shift[p];
+    dp.mk[p] = p < (int)passes ? (1u << a.pass_bits[p]) - 1 : 0u;
   }
   const bool hist = a.fuse_hist && g.key_bits <= 32;
 
@@ -78,7 +160,6 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
   const uint64_t t0 = (uint64_t)blockIdx.x * per;
   const uint64_t t1 = min(t0 + per, a.n_gen_tiles);
   int cur_rank = -1;
-  const uint64_t cmask = g.cbits >= 64 ? ~0ull : ((1ull << g.cbits) - 1);
 
   uint32_t cur_tbl = 0xFFFFFFFFu;      // delay table staged in s_tbl / s_guide
   for (uint64_t tile = t0; tile < t1; ++tile) {
@@ -117,56 +198,24 @@ __global__ void __launch_bounds__(GEN_BLOCK) gen_kernel(BuildArgs a) {
 
     const uint64_t e0 = (tile - blk.tile_first) * (uint64_t)GEN_TILE;
     const uint32_t n = (uint32_t)min((uint64_t)GEN_TILE, blk.count - e0);
-    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-    // fixed in-degree: (target m, k) of this thread's first item, then incremental
-    uint64_t m = 0;
-    uint32_t k = 0;
-    if (P.rule == kRuleFixedIndegree) {
-      const uint64_t e = e0 + tid;
-      m = div_magic(e, P.K, P.magic_div);
-      k = (uint32_t)(e - m * P.K);
-    }
-    const uint64_t cstep = (uint64_t)blk.tstep * P.K;
-    uint64_t cm = ((uint64_t)blk.ti0 + m * blk.tstep) * P.K;   // counter of (target m, k = 0)
-    for (uint32_t i = tid; i < n; i += GEN_BLOCK) {
-      const uint64_t e = e0 + i;
-      const uint64_t c = P.rule == kRuleFixedIndegree ? cm + k : e;   // fixed total on one rank: draws
-      // the source: word x of the synapse's Philox block, or fixed (all-to-all: k;
-      // one-to-one: the target's index); the delay: word y
-      const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id,
-                                               kPurposeSynapse), key);
-      const uint32_t si = P.src_mode == 0 ? uniform_index(b.x, P.n_src)
-                                          : (P.src_mode == kSrcAll ? k : (uint32_t)c);
-      const uint32_t src = P.src_first + si * P.src_stride;
-      uint32_t sig = 0, s = src;
-      if (g.R > 1) {
-        s = (uint32_t)div_magic(src, g.R, g.magic_R);
-        sig = src - s * g.R;
-      }
-      const uint32_t slot = sig == blk.rank ? 0u : (sig < blk.rank ? sig + 1 : sig);
-      uint32_t d = P.d_const;
-      if (P.d_kind == 1) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
-      const uint64_t kk = ((uint64_t)slot << (g.sb + g.db)) | ((uint64_t)s << g.db) | d;
-      const uint64_t cid = a.pos_counters ? blk.out_base + e : P.cbase + c;
-      a.rec_a[blk.out_base + e] = (kk << g.cbits) | (cid & cmask);
-      if (hist) {
-        const uint32_t k32 = (uint32_t)kk;
-#pragma unroll
-        for (int p = 0; p < MAX_PASSES; ++p)
-          if (dmk[p]) atomicAdd(&s_hist[p][(k32 >> dsh[p]) & dmk[p]], 1u);
-      } else if (a.fuse_hist) {
-#pragma unroll
-        for (int p = 0; p < MAX_PASSES; ++p)
-          if (dmk[p]) atomicAdd(&s_hist[p][(uint32_t)(kk >> dsh[p]) & dmk[p]], 1u);
-      }
-      if (P.rule == kRuleFixedIndegree) {        // advance to item i + GEN_BLOCK
-        k += GEN_BLOCK;
-        while (k >= P.K) {
-          k -= (uint32_t)P.K;
-          cm += cstep;
-        }
-      }
-    }
+    // the item loop, specialised per source mode, delay kind and key form (block-uniform
+    // choices taken once per tile instead of once per synapse)
+    const bool fi = P.rule == kRuleFixedIndegree;
+    const int mode = !fi ? GenFixedTotal : (P.src_mode == kSrcAll ? GenAll
+                                          : (P.src_mode == kSrcOneToOne ? GenOneToOne : GenRandom));
+    const bool one32 = g.R == 1 && hist && !a.pos_counters;
+    const bool dtab = P.d_kind == 1;
+#define SNN_GEN_CASE(M_, D_, O_) \
+    if (mode == M_ && dtab == D_ && one32 == O_) gen_items<M_, D_, O_>(a, blk, P, s_tbl, s_guide, s_hist, e0, n, dp, a.fuse_hist);
+    SNN_GEN_CASE(GenRandom, true, true) SNN_GEN_CASE(GenRandom, true, false)
+    SNN_GEN_CASE(GenRandom, false, true) SNN_GEN_CASE(GenRandom, false, false)
+    SNN_GEN_CASE(GenAll, true, true) SNN_GEN_CASE(GenAll, true, false)
+    SNN_GEN_CASE(GenAll, false, true) SNN_GEN_CASE(GenAll, false, false)
+    SNN_GEN_CASE(GenOneToOne, true, true) SNN_GEN_CASE(GenOneToOne, true, false)
+    SNN_GEN_CASE(GenOneToOne, false, true) SNN_GEN_CASE(GenOneToOne, false, false)
+    SNN_GEN_CASE(GenFixedTotal, true, true) SNN_GEN_CASE(GenFixedTotal, true, false)
+    SNN_GEN_CASE(GenFixedTotal, false, true) SNN_GEN_CASE(GenFixedTotal, false, false)
+#undef SNN_GEN_CASE
   }
   __syncthreads();
   if (cur_rank >= 0) {
@@ -1031,6 +1080,133 @@ __global__ void __launch_bounds__(256) finalize_kernel(BuildArgs a, const uint64
   }
 }
 
+// The projection a run of counters belongs to, held in registers while the counters of
+// consecutive records stay inside it (one-rank finalize).
+struct ProjRegs {
+  uint64_t lo, hi;          // counters [lo, hi) of the projection
+  uint64_t K, magic;        // fixed in-degree K (or n_src for Bernoulli) and its divisor magic
+  uint2 key;                // Philox key (the projection seed)
+  uint32_t rule, proj_id, tgt_first, tgt_stride, w_kind, idx;
+  float w_mean, w_sd;
+};
+
+__device__ __forceinline__ void load_proj_regs(const BuildArgs& a, uint64_t cidx, ProjRegs& q) {
+  const uint32_t p = upper_bound_u64(a.cbase_sorted, a.nproj, cidx) - 1;
+  const DevProj& P = a.projs[p];
+  q.lo = a.cbase_sorted[p];
+  q.hi = p + 1 < a.nproj ? a.cbase_sorted[p + 1] : ~0ull;
+  q.rule = P.rule;
+  q.K = P.rule == kRuleFixedIndegree ? P.K : (uint64_t)P.n_src;
+  q.magic = P.magic_div;
+  q.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+  q.proj_id = P.proj_id;
+  q.tgt_first = P.tgt_first;
+  q.tgt_stride = P.tgt_stride;
+  q.w_kind = P.w_kind;
+  q.w_mean = P.w_mean;
+  q.w_sd = P.w_sd;
+  q.idx = p;
+}
+
+// Finalize on one rank (no rank slots, counters as record ids): the same outputs as
+// finalize_kernel with the per-record work cut to the decode itself.  The row of a
+// record is its source; each projection's fields stay in registers while consecutive
+// records keep to its counters.  WF: weight format (0 fp32, 1 bf16, 2 fp16 with a
+// per-source scale).
+template <int WF>
+__global__ void __launch_bounds__(256) finalize_one_rank_kernel(BuildArgs a, const uint64_t* __restrict__ rec,
+                                                                uint64_t E, uint32_t vec) {
+  const Geom g = a.g;
+  const uint32_t cbits = g.cbits, db = g.db;
+  const uint64_t cmask = cbits >= 64 ? ~0ull : ((1ull << cbits) - 1);
+  const uint32_t smask = (uint32_t)((1ull << g.sb) - 1);
+  const uint32_t dmask = (1u << db) - 1;
+  const uint32_t N = g.N;
+  uint64_t* __restrict__ dn = a.dense;
+  const uint64_t nq = (E + FIN_Q - 1) / FIN_Q;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  ProjRegs q;
+  q.lo = 0;
+  q.hi = 0;                       // an empty range: the first record loads its projection
+  for (uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += stride) {
+    const uint64_t i0 = qi * FIN_Q;
+    const bool full = vec && i0 + FIN_Q <= E;
+    uint64_t r[FIN_Q];
+    if (full) {
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(rec + i0);
+      const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(rec + i0 + 2);
+      r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < FIN_Q; ++j) r[j] = i0 + j < E ? rec[i0 + j] : 0ull;
+    }
+    int64_t prow = i0 > 0 ? (int64_t)((uint32_t)(rec[i0 - 1] >> (cbits + db)) & smask) : -1;
+    uint32_t tl[FIN_Q], wb[FIN_Q], dd[FIN_Q];
+    bool ok[FIN_Q];
+#pragma unroll
+    for (int j = 0; j < FIN_Q; ++j) {
+      const uint64_t i = i0 + j;
+      ok[j] = false;
+      tl[j] = 0; wb[j] = 0; dd[j] = 0;
+      if (i >= E) continue;
+      const uint64_t key = r[j] >> cbits;
+      const uint64_t cidx = r[j] & cmask;
+      const uint32_t row = (uint32_t)(key >> db) & smask;
+      if ((key >> db) > smask || row >= N) {     // corrupt record: flag it, write nothing for it
+        atomicOr(a.err, kErrBounds);
+        prow = (int64_t)N;
+        continue;
+      }
+      for (int64_t x = prow + 1; x <= (int64_t)row; ++x) dn[x] = i;
+      if (i == E - 1)
+        for (uint64_t x = (uint64_t)row + 1; x <= N; ++x) dn[x] = E;
+      prow = row;
+      if (cidx - q.lo >= q.hi - q.lo) load_proj_regs(a, cidx, q);
+      const uint64_t c = cidx - q.lo;
+      uint32_t t;
+      if (q.rule == kRuleFixedTotal) t = fixed_total_target(a.projs[q.idx], c);
+      else t = q.tgt_first + (uint32_t)div_magic(c, q.K, q.magic) * q.tgt_stride;
+      tl[j] = t;
+      dd[j] = (uint32_t)key & dmask;
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), q.proj_id, kPurposeSynapse), q.key);
+      float w = q.w_mean;
+      if (q.w_kind != 0) {
+        const float u1 = u01(b.z), u2 = u01(b.w);
+        const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        w = fmaf(q.w_sd, z, q.w_mean);
+        w = q.w_mean >= 0.f ? fmaxf(w, 0.f) : fminf(w, 0.f);
+      }
+      if (WF == 0) {
+        wb[j] = __float_as_uint(w);
+      } else if (WF == 1) {
+        wb[j] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+      } else {
+        const float sc = a.row_scale_src ? a.row_scale_src[row] : 1.0f;
+        wb[j] = __half_as_ushort(__float2half_rn(w / sc));
+      }
+      ok[j] = true;
+    }
+    if (full && ok[0] && ok[1] && ok[2] && ok[3]) {
+      *reinterpret_cast<uint4*>(a.tgt + i0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+      *reinterpret_cast<uint32_t*>(a.d + i0) = dd[0] | (dd[1] << 8) | (dd[2] << 16) | (dd[3] << 24);
+      if (WF == 0)
+        *reinterpret_cast<uint4*>((uint32_t*)a.w + i0) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+      else
+        *reinterpret_cast<uint2*>((uint16_t*)a.w + i0) = make_uint2(wb[0] | (wb[1] << 16), wb[2] | (wb[3] << 16));
+    } else {
+#pragma unroll
+      for (int j = 0; j < FIN_Q; ++j) {
+        if (!ok[j]) continue;
+        const uint64_t i = i0 + j;
+        a.tgt[i] = tl[j];
+        a.d[i] = (uint8_t)dd[j];
+        if (WF == 0) ((uint32_t*)a.w)[i] = wb[j];
+        else ((uint16_t*)a.w)[i] = (uint16_t)wb[j];
+      }
+    }
+  }
+}
+
 __global__ void fill_empty_segments(uint64_t* dense, const uint64_t* seg_start, uint32_t seg0, uint32_t nseg,
                                     uint32_t N) {
   const uint64_t total = (uint64_t)nseg * (N + 1);
@@ -1052,7 +1228,13 @@ cudaError_t launch_finalize(const BuildArgs& a, const uint64_t* rec, uint64_t E,
   const uint64_t grid = std::min<uint64_t>((nq + 255) / 256, (uint64_t)a.num_sms * 16);
   // vector loads and stores need 16-byte aligned bases (quad starts are multiples of 4)
   const uint32_t vec = (((uintptr_t)rec | (uintptr_t)a.tgt | (uintptr_t)a.w | (uintptr_t)a.d) & 15u) == 0;
-  finalize_kernel<<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
+  if (a.g.R == 1 && !a.pos_counters && a.dense_seg0 == 0 && a.dense_nseg == 1) {
+    if (a.w_format == 0) finalize_one_rank_kernel<0><<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
+    else if (a.w_format == 1) finalize_one_rank_kernel<1><<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
+    else finalize_one_rank_kernel<2><<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
+  } else {
+    finalize_kernel<<<(unsigned)grid, 256, 0, st>>>(a, rec, E, vec);
+  }
   return cudaGetLastError();
 }
 

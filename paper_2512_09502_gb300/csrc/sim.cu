@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) update_kernel(SimArgs a, uint32_
   for (uint32_t i = tid; i < a.poisson_tbl_len && i < 256; i += UPD_BLOCK) s_tbl[i] = a.poisson_tbl[i];
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
   for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
-  const uint32_t slot = n & a.ring_mask;
+  const uint32_t slot = n % a.ring_slots;
   float* rex = a.ring + ((uint64_t)slot * a.n_rec) * a.ring_stride;
   float* rin = rex + a.ring_stride;
   const bool two = a.n_rec == 2;
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(UPD_BLOCK, 4) step_update_kernel(SimArgs a, ui
   for (uint32_t i = tid; i < a.npops && i < 64; i += UPD_BLOCK) s_pop[i] = a.pops[i];
   for (uint32_t i = tid; i < a.ndrives && i < MAX_SMEM_DRIVES; i += UPD_BLOCK) s_dr[i] = a.drives[i];
   if (post && blockIdx.x == 0 && tid == 0) a.n_work[(n + 2) % 3] = 0;
-  float* rex = a.ring + ((uint64_t)(n & a.ring_mask) * a.n_rec) * a.ring_stride;
+  float* rex = a.ring + ((uint64_t)(n % a.ring_slots) * a.n_rec) * a.ring_stride;
   float* rin = rex + a.ring_stride;
   const bool two = a.n_rec == 2;
   const uint32_t nq = (a.N + UPD_Q - 1) / UPD_Q;
@@ -524,9 +524,10 @@ __device__ __forceinline__ float load_w<__half>(const __half* w, uint64_t e, uin
 }
 
 // Events lo + first, lo + first + stride, ... < hi of one row: DEL_ILP events per thread
-// are loaded before their reductions are issued.
+// are loaded before their reductions are issued.  nb = step mod D: an event of delay d
+// (1 <= d < D) lands in slot nb + d, less D when that passes the ring's end.
 template <typename WT, int STRIDE>
-__device__ __forceinline__ void deliver_span(const SimArgs& a, const WT* __restrict__ w, uint32_t n,
+__device__ __forceinline__ void deliver_span(const SimArgs& a, const WT* __restrict__ w, uint32_t nb,
                                              uint64_t lo, uint64_t hi, uint32_t first, uint32_t stride,
                                              uint32_t toff, float sc, uint64_t pol_stream, uint64_t pol_ring) {
   float* __restrict__ ring = a.ring;
@@ -548,7 +549,8 @@ __device__ __forceinline__ void deliver_span(const SimArgs& a, const WT* __restr
       const uint64_t e = e0 + (uint64_t)k * st;
       if (e < hi) {
         if (tt[k] < a.N) {
-          const uint32_t slot = (n + dd[k]) & a.ring_mask;
+          uint32_t slot = nb + dd[k];
+          if (slot >= a.ring_slots) slot -= a.ring_slots;
           const uint32_t rec = (a.n_rec == 2 && ww[k] < 0.f) ? 1u : 0u;
           red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[k], ww[k], pol_ring);
         } else {
@@ -572,6 +574,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
   pdl_wait();                      // the step's list is complete
   pdl_trigger();
   const uint32_t n = __ldcg(a.step) + k_step;
+  const uint32_t nb = n % a.ring_slots;
   const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
   const uint32_t nitems = __ldcg(a.n_work + li);
   const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_kernel(SimArgs a, const WT*
     const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
     const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
     const uint32_t toff = taus ? a.rank_off[__ldcg(taus + si)] : 0u;   // first neuron position of the row's rank
-    deliver_span<WT, DEL_BLOCK>(a, w, n, lo, hi, threadIdx.x, DEL_BLOCK, toff, sc, pol_stream, pol_ring);
+    deliver_span<WT, DEL_BLOCK>(a, w, nb, lo, hi, threadIdx.x, DEL_BLOCK, toff, sc, pol_stream, pol_ring);
     if (sl == 0 && threadIdx.x == 0) atomicAdd(a.n_events, (unsigned long long)len);   // a few per CTA
   }
 }
@@ -600,6 +603,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, cons
   pdl_wait();                      // the step's list is complete
   pdl_trigger();
   const uint32_t n = __ldcg(a.step) + k_step;
+  const uint32_t nb = n % a.ring_slots;
   const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
   const uint32_t nitems = __ldcg(a.n_work + li);
   const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
@@ -623,7 +627,7 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, cons
       if (a.row_scale) sc = a.row_scale[row];
       if (sl == 0) events += hi - lo;
     }
-    deliver_span<WT, 0>(a, w, n, lo, hi, sl, L, toff, sc, pol_stream, pol_ring);
+    deliver_span<WT, 0>(a, w, nb, lo, hi, sl, L, toff, sc, pol_stream, pol_ring);
   }
   add_events(a, events);
 }

@@ -12,7 +12,7 @@ struct SimArgs {
   const DevPop* pops; uint32_t npops;
   const DevDrive* drives; uint32_t ndrives;
   const uint32_t* poisson_tbl; uint32_t poisson_tbl_len;
-  float* ring; uint32_t ring_mask;            // [D][n_rec][ring_stride]
+  float* ring; uint32_t ring_slots;           // [D][n_rec][ring_stride], D = largest delay + 1
   uint32_t ring_stride;                       // N rounded up to a multiple of 4
   uint32_t n_rec;                             // 2 receptors, or 1 when tau_ex == tau_in
   uint32_t* step;                             // device step counter (first step of a batch)
