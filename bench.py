@@ -316,6 +316,8 @@ def run_ours(args):
         if getattr(args, k):
             knobs[k] = getattr(args, k)
     extra = {"xi": args.xi} if args.xi else {}
+    if args.deliver_mode:
+        extra["deliver_mode"] = args.deliver_mode
 
     def one(fmt, sim_steps, profile=False):
         ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
@@ -457,7 +459,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "neurons": net.n_neurons, "synapses": s0["n_synapses"],
                        "sim_steps": args.sim_steps, "dt_ms": net.dt, "drive_hz": net.drives[0].rate_hz if net.drives else 0.0,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "n_ranks": net.n_ranks, "l2": "working set (connection layout) far larger than L2"},
+                       "n_ranks": net.n_ranks, "l2": "working set (connection layout) far larger than L2",
+                       "deliver_mode": "direct loads" if args.deliver_mode else "staged bulk copies"},
             "components": {"synapses_built_per_s": syn_per_s, "synaptic_events_per_s": ev_per_s,
                            "construct_ms": s0["t_calibrate_ms"], "simulate_ms": s0["t_simulate_ms"],
                            "generate_ms": s0["t_generate_ms"], "sort_ms": s0["t_sort_ms"],
@@ -500,6 +503,8 @@ def main():
     ap.add_argument("--sort-items", dest="sort_items", type=int, default=0)
     ap.add_argument("--deliver-ctas", dest="deliver_ctas_per_sm", type=int, default=0)
     ap.add_argument("--xi", type=float, default=0.0)
+    ap.add_argument("--deliver-mode", dest="deliver_mode", type=int, default=0,
+                    help="0: staged chunks (bulk copies), 1: direct loads")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -135,6 +135,10 @@ typedef struct snn_config {
      connections have empty rows.  xi <= 0 (the default) flags used sources only; the
      paper uses xi = 1.  The connections themselves do not depend on xi. */
   double xi;
+  int32_t deliver_mode;        /* long rows: 0 = chunks staged in shared memory by bulk
+                                  asynchronous copies while earlier chunks are delivered
+                                  (when the layout arrays are 16-byte aligned); 1 = each
+                                  thread loads its events directly                      */
 } snn_config;
 
 /* iaf_psc_exp parameters; potentials in mV relative to E_L = 0, C_m in pF, times in

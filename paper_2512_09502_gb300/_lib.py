@@ -47,7 +47,8 @@ class snn_config(C.Structure):
                 ("exchange", C.c_int32), ("use_graph", C.c_int32),
                 ("spike_log_capacity", C.c_uint64), ("radix_bits", C.c_int32), ("device", C.c_int32),
                 ("profile_kernels", C.c_int32), ("sort_items", C.c_int32), ("deliver_ctas_per_sm", C.c_int32),
-                ("dry_run", C.c_int32), ("dry_run_rank", C.c_uint32), ("xi", C.c_double)]
+                ("dry_run", C.c_int32), ("dry_run_rank", C.c_uint32), ("xi", C.c_double),
+                ("deliver_mode", C.c_int32)]
 
 
 class snn_iaf_psc_exp_params(C.Structure):
@@ -166,7 +167,8 @@ class Context:
                  exchange: str = "p2p", use_graph: bool = True, spike_log_capacity: int = 0,
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
                  stream: Optional[int] = None, profile_kernels: int = 0, sort_items: int = 0,
-                 deliver_ctas_per_sm: int = 0, dry_run_rank: Optional[int] = None, xi: float = 0.0):
+                 deliver_ctas_per_sm: int = 0, dry_run_rank: Optional[int] = None, xi: float = 0.0,
+                 deliver_mode: int = 0):
         self.lib = load()
         if not (radix_bits and sort_items and deliver_ctas_per_sm):
             from . import autotune        # tuned launch parameters, when a cache exists
@@ -178,7 +180,7 @@ class Context:
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
                          int(profile_kernels), sort_items, deliver_ctas_per_sm,
                          0 if dry_run_rank is None else 1, 0 if dry_run_rank is None else dry_run_rank,
-                         float(xi))
+                         float(xi), int(deliver_mode))
         self._allocator = allocator
         h = C.c_void_p()
         rc = self.lib.snn_create(C.byref(cfg), C.byref(allocator.struct) if allocator else None,

@@ -356,6 +356,7 @@ int snn_create(const snn_config* config, const snn_allocator* alloc, void* cuda_
       return SNN_EINVAL;
     if (!(config->xi == config->xi)) return SNN_EINVAL;    // NaN threshold
     if (config->profile_kernels < 0 || config->profile_kernels > 2) return SNN_EINVAL;
+    if (config->deliver_mode < 0 || config->deliver_mode > 1) return SNN_EINVAL;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) {
@@ -770,10 +771,12 @@ int snn_calibrate(snn_ctx* c) {
   dfree(c, bin_base);
 
   // ---- final layout ----
-  AL(c->d_tgt, std::max<uint64_t>(E, 1), "targets");
-  c->d_w = dalloc(c, std::max<uint64_t>(E, 1) * c->wbytes);
+  // the arrays hold 16 elements beyond the last synapse: the staged delivery copies
+  // whole 16-element groups (its chunk ends round up), and reads but ignores the rest
+  AL(c->d_tgt, E + 16, "targets");
+  c->d_w = dalloc(c, (E + 16) * c->wbytes);
   if (!c->d_w) return fail(c, SNN_ENOMEM, "allocation failed: weights");
-  AL(c->d_d, std::max<uint64_t>(E, 1), "delays");
+  AL(c->d_d, E + 16, "delays");
   AL(c->d_dense, (uint64_t)(dry ? 1 : R) * (N + 1), "row starts");
   if (c->cfg.weight_format == SNN_WEIGHT_F16) {
     // per source gid: power-of-two scale of the largest |mean| among its projections
@@ -908,10 +911,18 @@ int snn_calibrate(snn_ctx* c) {
   s.deliver_grid = (uint32_t)c->num_sms * (uint32_t)c->cfg.deliver_ctas_per_sm;
   s.update_grid = (uint32_t)c->num_sms * 8;
   s.lists = 2;
+  // staged delivery of long rows: bulk copies need 16-byte aligned array bases; its grid
+  // is at most what stays resident (CTAs take their items in a fixed order)
+  const bool aligned = (((uintptr_t)c->d_tgt | (uintptr_t)c->d_w | (uintptr_t)c->d_d) & 15u) == 0;
+  const int staged_per_sm = staged_deliver_ctas_per_sm((uint32_t)c->cfg.weight_format);
+  const bool staged = aligned && c->cfg.deliver_mode == 0 && staged_per_sm > 0;
+  s.staged_grid = (uint32_t)c->num_sms * (uint32_t)std::max(1, std::min(staged_per_sm, c->cfg.deliver_ctas_per_sm));
   if (R > 1) {
     int rc = setup_routing(c);
     if (rc != SNN_OK) return rc;
+    s.staged = staged && s.item_lanes == 0;
   } else {
+    s.staged = staged;
     // one rank: the neuron work of a step overlaps its delivery (two streams, lists
     // modulo 3); a small neuron grid leaves the delivery most of every SM
     c->ov = s;

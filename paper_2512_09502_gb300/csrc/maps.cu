@@ -771,6 +771,26 @@ __global__ void route_kernel(RouteArgs r, uint32_t k_step) {
 }
 }  // namespace
 
+namespace {
+// fp16 weights are stored as w / scale with a power-of-two scale per source neuron;
+// delivery multiplies by the scale of the row's source: for rank tau's local row s the
+// neuron s R + tau, for an image row the image's gid.  One entry per row start of the
+// concatenated per-rank rows (the sentinel after each rank's rows gets 1).
+__global__ void row_scale_fill(const uint64_t* rows_off, uint32_t R, const uint32_t* M, const uint64_t* img_first,
+                               const uint32_t* img_gid, const float* scale_src, float* out, uint64_t total) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = upper_bound_u64(rows_off, R + 1, x) - 1;
+    const uint64_t r = x - rows_off[w];
+    const uint64_t n_img = rows_off[w + 1] - rows_off[w] - 1 - M[w];
+    float v = 1.0f;
+    if (r < M[w]) v = scale_src[r * R + w];
+    else if (r - M[w] < n_img) v = scale_src[img_gid[img_first[w] + (r - M[w])]];
+    out[x] = v;
+  }
+}
+}  // namespace
+
 int setup_routing(snn_ctx* c) {
   MapsState& m = ctx_maps(c);
   SimArgs& s = ctx_sim(c);
@@ -806,6 +826,15 @@ int setup_routing(snn_ctx* c) {
   MCK(cudaMemsetAsync(r.n_work, 0, 8, ctx_stream(c)));
   s.work = r.work; s.n_work = r.n_work; s.work_stride = r.work_cap; s.work_rank = r.work_tau;
   s.rows = m.rows; s.rows_off = m.d_rows_off; s.rank_off = m.d_rank_off;
+  if (ctx_scale_src(c)) {
+    const uint64_t total = m.rows_off.back();
+    float* rs = alloc_n<float>(c, std::max<uint64_t>(total, 1));
+    if (!rs) return ctx_fail(c, SNN_ENOMEM, "routing: allocation failed");
+    row_scale_fill<<<grid_for(c, total), MB, 0, ctx_stream(c)>>>(m.d_rows_off, m.R, m.d_M, m.d_img_first, m.img_gid,
+                                                                 ctx_scale_src(c), rs, total);
+    MCK(cudaGetLastError());
+    s.row_scale = rs;
+  }
   // rows average E / (local rows + images); short rows are delivered by lane groups
   const uint64_t n_rows = m.rows_off.empty() ? 0 : m.rows_off.back();
   const double avg = n_rows ? (double)ctx_geom_synapses(c) / (double)n_rows : 0.0;

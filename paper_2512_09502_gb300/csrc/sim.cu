@@ -632,6 +632,180 @@ __global__ void __launch_bounds__(DEL_BLOCK) deliver_rows_kernel(SimArgs a, cons
   add_events(a, events);
 }
 
+// ---------------------------------------------------------------------------
+// Delivery with staged rows: bulk asynchronous copies (cp.async.bulk, completed on an
+// mbarrier) move each chunk of a row's targets, weights and delays into shared memory
+// while the chunks before it are being delivered.  Warp 0 is the producer: lane 0 walks
+// the CTA's (row, slice) items, splits each slice into chunks of up to TD_CHUNK events,
+// and issues three copies per chunk into the next free stage.  Warps 1-7 consume the
+// stages in order and issue the reductions.  Every wait is bounded: a wait that gives up
+// sets kErrTimeout and ends its thread's loop; the producer then waits (bounded again)
+// for the copies it issued before it returns.
+constexpr int TD_STAGES = 4;
+constexpr int TD_CHUNK = 1024;                // events per staged chunk
+constexpr int TD_CAP = TD_CHUNK + 32;         // chunk start rounded down, end up, to 16 events
+constexpr int TD_BLOCK = 256;
+constexpr int TD_CONSUMER_WARPS = TD_BLOCK / 32 - 1;
+constexpr uint32_t TD_SPIN = 1u << 22;
+
+template <typename WT>
+struct __align__(128) TdStage {
+  uint32_t tgt[TD_CAP];
+  WT w[TD_CAP];
+  uint8_t d[TD_CAP];
+};
+struct TdMeta {
+  uint32_t off, n, toff, done;   // first event's index in the stage, events, rank offset, end marker
+  float sc;                      // weight scale of the row (fp16 format)
+};
+template <typename WT>
+struct TdSmem {
+  TdStage<WT> st[TD_STAGES];
+  TdMeta meta[TD_STAGES];
+  unsigned long long full[TD_STAGES], empty[TD_STAGES];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_parity(unsigned long long* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete; false when it gave up (or
+// another wait of the grid already did).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, uint32_t* err) {
+  for (uint32_t spins = 0; !mbar_test_parity(b, parity); ++spins) {
+    if (spins > TD_SPIN || (*(volatile uint32_t*)err & kErrTimeout)) {
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                          uint64_t pol) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+
+template <typename WT>
+__device__ __forceinline__ float stage_w(const WT* w, uint32_t i);
+template <>
+__device__ __forceinline__ float stage_w<float>(const float* w, uint32_t i) { return w[i]; }
+template <>
+__device__ __forceinline__ float stage_w<__nv_bfloat16>(const __nv_bfloat16* w, uint32_t i) {
+  return __bfloat162float(w[i]);
+}
+template <>
+__device__ __forceinline__ float stage_w<__half>(const __half* w, uint32_t i) { return __half2float(w[i]); }
+
+template <typename WT>
+__global__ void __launch_bounds__(TD_BLOCK) deliver_staged_kernel(SimArgs a, const WT* __restrict__ w,
+                                                                  uint32_t k_step) {
+  __shared__ TdSmem<WT> sm;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < TD_STAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], TD_CONSUMER_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();                      // the step's list is complete
+  pdl_trigger();
+  const uint32_t n = __ldcg(a.step) + k_step;
+  const uint32_t nb = n % a.ring_slots;
+  const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
+
+  if (warp == 0) {
+    if (lane != 0) return;
+    // ---- producer ----
+    const uint32_t nitems = __ldcg(a.n_work + li);
+    const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
+    const uint32_t* taus = a.work_rank ? a.work_rank + (uint64_t)li * a.work_stride : nullptr;
+    const uint32_t slices = a.slices;
+    const uint64_t total = (uint64_t)nitems * slices;
+    const uint64_t pol = policy_evict_first();
+    uint32_t k = 0;
+    bool ok = true;
+    for (uint64_t it = blockIdx.x; ok && it < total; it += gridDim.x) {
+      const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
+      const uint32_t row = __ldcg(items + si);
+      const uint64_t ra = a.rows[row], rb = a.rows[row + 1];
+      const uint64_t len = rb - ra;
+      const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
+      const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
+      const uint32_t toff = taus ? a.rank_off[__ldcg(taus + si)] : 0u;
+      if (sl == 0) atomicAdd(a.n_events, (unsigned long long)len);
+      for (uint64_t c0 = lo; c0 < hi; c0 += TD_CHUNK) {
+        const uint64_t c1 = min(c0 + (uint64_t)TD_CHUNK, hi);
+        const uint32_t s = k % TD_STAGES, r = k / TD_STAGES;
+        if (r > 0 && !mbar_wait(&sm.empty[s], (r - 1) & 1, a.err)) { ok = false; break; }
+        const uint64_t base = c0 & ~15ull, end = (c1 + 15) & ~15ull;
+        const uint32_t nn = (uint32_t)(end - base);
+        sm.meta[s] = TdMeta{(uint32_t)(c0 - base), (uint32_t)(c1 - c0), toff, 0u, sc};
+        mbar_arrive_expect_tx(&sm.full[s], nn * (4u + (uint32_t)sizeof(WT) + 1u));
+        bulk_load(sm.st[s].tgt, a.tgt + base, nn * 4u, &sm.full[s], pol);
+        bulk_load(sm.st[s].w, w + base, nn * (uint32_t)sizeof(WT), &sm.full[s], pol);
+        bulk_load(sm.st[s].d, a.d + base, nn, &sm.full[s], pol);
+        ++k;
+      }
+    }
+    if (ok) {                      // end marker: a stage without copies
+      const uint32_t s = k % TD_STAGES, r = k / TD_STAGES;
+      if (r == 0 || mbar_wait(&sm.empty[s], (r - 1) & 1, a.err)) {
+        sm.meta[s] = TdMeta{0u, 0u, 0u, 1u, 1.0f};
+        mbar_arrive(&sm.full[s]);
+        return;
+      }
+    }
+    // gave up: wait for every copy still in flight before the CTA's shared memory goes
+    for (uint32_t q = k > TD_STAGES ? k - TD_STAGES : 0; q < k; ++q) {
+      uint32_t spins = 0;
+      while (!mbar_test_parity(&sm.full[q % TD_STAGES], (q / TD_STAGES) & 1) && ++spins < TD_SPIN) __nanosleep(32);
+    }
+    return;
+  }
+  // ---- consumers ----
+  const uint64_t pol_ring = policy_evict_last();
+  const uint32_t ctid = tid - 32;
+  float* __restrict__ ring = a.ring;
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t s = k % TD_STAGES;
+    if (!mbar_wait(&sm.full[s], (k / TD_STAGES) & 1, a.err)) return;
+    const TdMeta m = sm.meta[s];
+    if (m.done) return;
+    const TdStage<WT>& st = sm.st[s];
+    for (uint32_t j = ctid; j < m.n; j += TD_BLOCK - 32) {
+      const uint32_t i = m.off + j;
+      const uint32_t t = st.tgt[i] + m.toff;
+      const float wv = stage_w<WT>(st.w, i) * m.sc;
+      if (t < a.N) {
+        uint32_t slot = nb + st.d[i];
+        if (slot >= a.ring_slots) slot -= a.ring_slots;
+        const uint32_t rec = (a.n_rec == 2 && wv < 0.f) ? 1u : 0u;
+        red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + t, wv, pol_ring);
+      } else {
+        atomicOr(a.err, kErrBounds);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.empty[s]);
+  }
+}
+
 __global__ void advance_step_kernel(uint32_t* step, uint32_t by) { *step += by; }
 
 __global__ void init_state_kernel(SimArgs a, const float* v0) {
@@ -655,6 +829,8 @@ template <typename WT>
 static cudaError_t launch_deliver_t(const SimArgs& a, const WT* w, uint32_t k_step, cudaStream_t st, bool pdl) {
   const dim3 grid((unsigned)a.deliver_grid);
   if (a.item_lanes) return launch_pdl(deliver_rows_kernel<WT>, grid, dim3(DEL_BLOCK), st, pdl, a, w, k_step);
+  if (a.staged) return launch_pdl(deliver_staged_kernel<WT>, dim3((unsigned)a.staged_grid), dim3(TD_BLOCK), st, pdl,
+                                  a, w, k_step);
   return launch_pdl(deliver_kernel<WT>, grid, dim3(DEL_BLOCK), st, pdl, a, w, k_step);
 }
 
@@ -674,6 +850,17 @@ cudaError_t launch_step_update(const SimArgs& a, uint32_t k_step, uint32_t mode,
 cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st) {
   advance_step_kernel<<<1, 1, 0, st>>>(a.step, by);
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the staged delivery (its shared memory bounds them).
+int staged_deliver_ctas_per_sm(uint32_t w_format) {
+  int n = 0;
+  cudaError_t e;
+  if (w_format == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, deliver_staged_kernel<float>, TD_BLOCK, 0);
+  else if (w_format == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, deliver_staged_kernel<__nv_bfloat16>, TD_BLOCK, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, deliver_staged_kernel<__half>, TD_BLOCK, 0);
+  return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st) {

@@ -32,6 +32,8 @@ struct SimArgs {
   uint32_t deliver_grid, update_grid;
   uint32_t lists;                             // spike / work lists cycled: 2, or 3 (overlapped steps)
   uint32_t* err;                              // device error word (kErrBounds: an event's target out of range)
+  uint32_t staged;                            // long rows: chunks staged in shared memory by bulk copies
+  uint32_t staged_grid;                       // CTAs of the staged delivery (all resident at once)
 };
 
 // Overlapped steps (one rank): the neuron work of step k and the delivery of step k run
@@ -72,5 +74,6 @@ cudaError_t launch_update(const SimArgs& a, uint32_t k_step, cudaStream_t st, bo
 cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st, bool pdl);
 cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st);
 cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st);
+int staged_deliver_ctas_per_sm(uint32_t w_format);
 
 }  // namespace snn
