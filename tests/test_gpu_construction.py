@@ -131,3 +131,32 @@ def test_multi_area_batched_blocks():
     net = wl.multi_area(seed=1234, n_areas=8, area_mean=400.0)
     assert len(net.projections) > 8 * 64
     _check(net)
+
+
+def _runs(row_ptr, key):
+    """Starts of the maximal runs of equal `key` inside every row (row starts included)."""
+    starts = set(int(x) for x in row_ptr[:-1] if x < row_ptr[-1])
+    starts.update(int(i) for i in np.nonzero(key[1:] != key[:-1])[0] + 1)
+    return np.array(sorted(starts), dtype=np.int64)
+
+
+@pytest.mark.parametrize("R", [1, 3])
+def test_delay_runs_recovered_from_row_starts_and_delays(R):
+    """The layout stores no per-(source, delay) run offsets: every row is non-decreasing in
+    its delays, so its runs are its maximal stretches of equal delay.  The run starts
+    recovered that way from the device's row starts and delay array equal the (source,
+    delay) run starts of the oracle's layout, on one rank and on three."""
+    net = wl.balanced(1200, 300, 60, 15, wl.DELAY_NORMAL, seed=17, n_ranks=R)
+    ctx = gpu_build(net)
+    _, ref = oracle_layout(net)
+    for tau in range(R):
+        got = ctx.get_connections(tau)
+        rp, d = got["row_ptr"], got["d"].astype(np.int64)
+        for r in range(len(rp) - 1):
+            assert np.all(np.diff(d[rp[r]:rp[r + 1]]) >= 0), (tau, r)
+        row_of = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        gpu_runs = _runs(rp, row_of * 1024 + d)
+        rk = ref["ranks"][tau]
+        oracle_runs = _runs(rk["row_ptr"], rk["src"].astype(np.int64) * 1024 + rk["d"])
+        np.testing.assert_array_equal(gpu_runs, oracle_runs)
+    ctx.destroy()
