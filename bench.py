@@ -125,17 +125,15 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# DRAM bytes per unit: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture,
-# divided by the units the captured launch processed, with the source file that was
-# measured (sha256[:16] of the whole file at capture time, so that a change anywhere in
-# the file, inlined helpers included, retires the figure).  The construction figures come
-# from the 112.5M-synapse case (bench workload construction_112m): these kernels stream
-# their records, so DRAM bytes grow in proportion to the records of a launch and the
-# per-unit figure scales to the full-size launch.
+# DRAM bytes per unit: dram__bytes_read.sum + dram__bytes_write.sum of a one-pass ncu
+# capture of the timed step at full size (--cache-control none), divided by the units
+# the captured launch processed, with the source file that was measured (sha256[:16] of
+# the whole file at capture time, so that a change anywhere in the file, inlined helpers
+# included, retires the figure).
 TRAFFIC = {
-    "gen_kernel": {"bytes_per_unit": 7.477, "source": "build.cu", "file_sha": "95e468867498e6a0"},
-    "onesweep_pass": {"bytes_per_unit": 16.22, "source": "build.cu", "file_sha": "95e468867498e6a0"},
-    "finalize_kernel": {"bytes_per_unit": 16.62, "source": "build.cu", "file_sha": "95e468867498e6a0"},
+    "gen_kernel": {"bytes_per_unit": 8.02, "source": "build.cu", "file_sha": "95e468867498e6a0"},
+    "onesweep_pass": {"bytes_per_unit": 16.66, "source": "build.cu", "file_sha": "95e468867498e6a0"},
+    "finalize_kernel": {"bytes_per_unit": 17.18, "source": "build.cu", "file_sha": "95e468867498e6a0"},
 }
 
 
