@@ -308,14 +308,15 @@ def run_ours(args):
     tuned = autotune.load()
     if args.autotune and (tuned is None or tuned.get("network") != net.name):
         tuned = autotune.tune(net, allocator=alloc, stream=stream.cuda_stream, device=local,
-                              sim_steps=min(args.sim_steps, 1000))
-    knobs = {k: int(tuned[k]) for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm")} if tuned else {}
+                              sim_steps=min(args.sim_steps, 2000))
+    knobs = {k: int(tuned[k]) for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm", "deliver_mode")
+             if k in tuned} if tuned else {}
     for k in ("radix_bits", "sort_items", "deliver_ctas_per_sm"):
         if getattr(args, k):
             knobs[k] = getattr(args, k)
     extra = {"xi": args.xi} if args.xi else {}
-    if args.deliver_mode:
-        extra["deliver_mode"] = args.deliver_mode
+    if args.deliver_mode is not None:
+        knobs["deliver_mode"] = args.deliver_mode
 
     def one(fmt, sim_steps, profile=False):
         ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
@@ -458,7 +459,7 @@ def run_ours(args):
                        "sim_steps": args.sim_steps, "dt_ms": net.dt, "drive_hz": net.drives[0].rate_hz if net.drives else 0.0,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "n_ranks": net.n_ranks, "l2": "working set (connection layout) far larger than L2",
-                       "deliver_mode": "direct loads" if args.deliver_mode else "staged bulk copies"},
+                       "deliver_mode": "direct loads" if knobs.get("deliver_mode", 0) else "staged bulk copies"},
             "components": {"synapses_built_per_s": syn_per_s, "synaptic_events_per_s": ev_per_s,
                            "construct_ms": s0["t_calibrate_ms"], "simulate_ms": s0["t_simulate_ms"],
                            "generate_ms": s0["t_generate_ms"], "sort_ms": s0["t_sort_ms"],
@@ -501,8 +502,8 @@ def main():
     ap.add_argument("--sort-items", dest="sort_items", type=int, default=0)
     ap.add_argument("--deliver-ctas", dest="deliver_ctas_per_sm", type=int, default=0)
     ap.add_argument("--xi", type=float, default=0.0)
-    ap.add_argument("--deliver-mode", dest="deliver_mode", type=int, default=0,
-                    help="0: staged chunks (bulk copies), 1: direct loads")
+    ap.add_argument("--deliver-mode", dest="deliver_mode", type=int, default=None,
+                    help="0: staged chunks (bulk copies), 1: direct loads (default: tuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

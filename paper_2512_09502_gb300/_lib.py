@@ -168,7 +168,7 @@ class Context:
                  radix_bits: int = 0, device: int = 0, allocator: Optional[TorchAllocator] = None,
                  stream: Optional[int] = None, profile_kernels: int = 0, sort_items: int = 0,
                  deliver_ctas_per_sm: int = 0, dry_run_rank: Optional[int] = None, xi: float = 0.0,
-                 deliver_mode: int = 0):
+                 deliver_mode: Optional[int] = None):
         self.lib = load()
         if not (radix_bits and sort_items and deliver_ctas_per_sm):
             from . import autotune        # tuned launch parameters, when a cache exists
@@ -176,6 +176,10 @@ class Context:
             radix_bits = radix_bits or int(tuned.get("radix_bits", 0))
             sort_items = sort_items or int(tuned.get("sort_items", 0))
             deliver_ctas_per_sm = deliver_ctas_per_sm or int(tuned.get("deliver_ctas_per_sm", 0))
+            if deliver_mode is None:
+                deliver_mode = int(tuned.get("deliver_mode", 0))
+        if deliver_mode is None:
+            deliver_mode = 0
         cfg = snn_config(dt, n_ranks, WEIGHT_FORMATS[weight_format], 0 if exchange == "p2p" else 1,
                          1 if use_graph else 0, spike_log_capacity, radix_bits, device,
                          int(profile_kernels), sort_items, deliver_ctas_per_sm,

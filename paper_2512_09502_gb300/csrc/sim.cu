@@ -646,6 +646,8 @@ constexpr int TD_CHUNK = 1024;                // events per staged chunk
 constexpr int TD_CAP = TD_CHUNK + 32;         // chunk start rounded down, end up, to 16 events
 constexpr int TD_BLOCK = 256;
 constexpr int TD_CONSUMER_WARPS = TD_BLOCK / 32 - 1;
+constexpr uint32_t TD_CONSUMERS = TD_BLOCK - 32;    // consumer threads
+constexpr int TD_ILP = 4;                           // events per consumer thread in flight
 constexpr uint32_t TD_SPIN = 1u << 22;
 
 template <typename WT>
@@ -730,7 +732,6 @@ __global__ void __launch_bounds__(TD_BLOCK) deliver_staged_kernel(SimArgs a, con
   const uint32_t li = a.lists == 3 ? n % 3 : n & 1;
 
   if (warp == 0) {
-    if (lane != 0) return;
     // ---- producer ----
     const uint32_t nitems = __ldcg(a.n_work + li);
     const uint32_t* items = a.work + (uint64_t)li * a.work_stride;
@@ -738,31 +739,51 @@ __global__ void __launch_bounds__(TD_BLOCK) deliver_staged_kernel(SimArgs a, con
     const uint32_t slices = a.slices;
     const uint64_t total = (uint64_t)nitems * slices;
     const uint64_t pol = policy_evict_first();
+    const uint64_t G = gridDim.x;
     uint32_t k = 0;
     bool ok = true;
-    for (uint64_t it = blockIdx.x; ok && it < total; it += gridDim.x) {
-      const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
-      const uint32_t row = __ldcg(items + si);
-      const uint64_t ra = a.rows[row], rb = a.rows[row + 1];
-      const uint64_t len = rb - ra;
-      const uint64_t lo = ra + len * sl / slices, hi = ra + len * (sl + 1) / slices;
-      const float sc = a.row_scale ? a.row_scale[row] : 1.0f;
-      const uint32_t toff = taus ? a.rank_off[__ldcg(taus + si)] : 0u;
-      if (sl == 0) atomicAdd(a.n_events, (unsigned long long)len);
-      for (uint64_t c0 = lo; c0 < hi; c0 += TD_CHUNK) {
-        const uint64_t c1 = min(c0 + (uint64_t)TD_CHUNK, hi);
-        const uint32_t s = k % TD_STAGES, r = k / TD_STAGES;
-        if (r > 0 && !mbar_wait(&sm.empty[s], (r - 1) & 1, a.err)) { ok = false; break; }
-        const uint64_t base = c0 & ~15ull, end = (c1 + 15) & ~15ull;
-        const uint32_t nn = (uint32_t)(end - base);
-        sm.meta[s] = TdMeta{(uint32_t)(c0 - base), (uint32_t)(c1 - c0), toff, 0u, sc};
-        mbar_arrive_expect_tx(&sm.full[s], nn * (4u + (uint32_t)sizeof(WT) + 1u));
-        bulk_load(sm.st[s].tgt, a.tgt + base, nn * 4u, &sm.full[s], pol);
-        bulk_load(sm.st[s].w, w + base, nn * (uint32_t)sizeof(WT), &sm.full[s], pol);
-        bulk_load(sm.st[s].d, a.d + base, nn, &sm.full[s], pol);
-        ++k;
+    for (uint64_t it0 = blockIdx.x; ok && it0 < total; it0 += 32 * G) {
+      // the bounds of the CTA's next 32 items, one per lane, loaded at once; lane 0 then
+      // issues their chunks in item order
+      const uint64_t it = it0 + (uint64_t)lane * G;
+      uint64_t lo = 0, hi = 0;
+      uint32_t toff = 0;
+      float sc = 1.0f;
+      if (it < total) {
+        const uint32_t si = (uint32_t)(it / slices), sl = (uint32_t)(it - (uint64_t)si * slices);
+        const uint32_t row = __ldcg(items + si);
+        const uint64_t ra = a.rows[row], rb = a.rows[row + 1];
+        const uint64_t len = rb - ra;
+        lo = ra + len * sl / slices;
+        hi = ra + len * (sl + 1) / slices;
+        if (a.row_scale) sc = a.row_scale[row];
+        if (taus) toff = a.rank_off[__ldcg(taus + si)];
+        if (sl == 0) atomicAdd(a.n_events, (unsigned long long)len);
       }
+      for (int l = 0; l < 32; ++l) {
+        const uint64_t lo_l = __shfl_sync(0xffffffffu, lo, l), hi_l = __shfl_sync(0xffffffffu, hi, l);
+        const uint32_t toff_l = __shfl_sync(0xffffffffu, toff, l);
+        const float sc_l = __shfl_sync(0xffffffffu, sc, l);
+        if (lane == 0 && ok) {
+          for (uint64_t c0 = lo_l; c0 < hi_l; c0 += TD_CHUNK) {
+            const uint64_t c1 = min(c0 + (uint64_t)TD_CHUNK, hi_l);
+            const uint32_t s = k % TD_STAGES, r = k / TD_STAGES;
+            if (r > 0 && !mbar_wait(&sm.empty[s], (r - 1) & 1, a.err)) { ok = false; break; }
+            const uint64_t base = c0 & ~15ull, end = (c1 + 15) & ~15ull;
+            const uint32_t nn = (uint32_t)(end - base);
+            sm.meta[s] = TdMeta{(uint32_t)(c0 - base), (uint32_t)(c1 - c0), toff_l, 0u, sc_l};
+            mbar_arrive_expect_tx(&sm.full[s], nn * (4u + (uint32_t)sizeof(WT) + 1u));
+            bulk_load(sm.st[s].tgt, a.tgt + base, nn * 4u, &sm.full[s], pol);
+            bulk_load(sm.st[s].w, w + base, nn * (uint32_t)sizeof(WT), &sm.full[s], pol);
+            bulk_load(sm.st[s].d, a.d + base, nn, &sm.full[s], pol);
+            ++k;
+          }
+        }
+        __syncwarp();
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     }
+    if (lane != 0) return;
     if (ok) {                      // end marker: a stage without copies
       const uint32_t s = k % TD_STAGES, r = k / TD_STAGES;
       if (r == 0 || mbar_wait(&sm.empty[s], (r - 1) & 1, a.err)) {
@@ -788,17 +809,34 @@ __global__ void __launch_bounds__(TD_BLOCK) deliver_staged_kernel(SimArgs a, con
     const TdMeta m = sm.meta[s];
     if (m.done) return;
     const TdStage<WT>& st = sm.st[s];
-    for (uint32_t j = ctid; j < m.n; j += TD_BLOCK - 32) {
-      const uint32_t i = m.off + j;
-      const uint32_t t = st.tgt[i] + m.toff;
-      const float wv = stage_w<WT>(st.w, i) * m.sc;
-      if (t < a.N) {
-        uint32_t slot = nb + st.d[i];
-        if (slot >= a.ring_slots) slot -= a.ring_slots;
-        const uint32_t rec = (a.n_rec == 2 && wv < 0.f) ? 1u : 0u;
-        red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + t, wv, pol_ring);
-      } else {
-        atomicOr(a.err, kErrBounds);
+    // TD_ILP events per thread read from the stage before their reductions are issued
+    for (uint32_t j0 = ctid; j0 < m.n; j0 += TD_ILP * TD_CONSUMERS) {
+      uint32_t tt[TD_ILP], dd[TD_ILP];
+      float ww[TD_ILP];
+#pragma unroll
+      for (int q = 0; q < TD_ILP; ++q) {
+        const uint32_t j = j0 + q * TD_CONSUMERS;
+        tt[q] = 0;
+        dd[q] = 0;
+        ww[q] = 0.f;
+        if (j < m.n) {
+          const uint32_t i = m.off + j;
+          tt[q] = st.tgt[i] + m.toff;
+          ww[q] = stage_w<WT>(st.w, i) * m.sc;
+          dd[q] = st.d[i];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TD_ILP; ++q) {
+        if (j0 + q * TD_CONSUMERS >= m.n) continue;
+        if (tt[q] < a.N) {
+          uint32_t slot = nb + dd[q];
+          if (slot >= a.ring_slots) slot -= a.ring_slots;
+          const uint32_t rec = (a.n_rec == 2 && ww[q] < 0.f) ? 1u : 0u;
+          red_add_keep(ring + ((uint64_t)slot * a.n_rec + rec) * a.ring_stride + tt[q], ww[q], pol_ring);
+        } else {
+          atomicOr(a.err, kErrBounds);
+        }
       }
     }
     __syncwarp();
