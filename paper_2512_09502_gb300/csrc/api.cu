@@ -125,11 +125,11 @@ struct snn_ctx {
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_steps = 0;
   bool capturing = false;
-  // overlapped steps (one rank): neuron work on st, delivery on st2, lists modulo 3
+  // overlapped steps (one rank): neuron work on st, deliveries on st2 / st3, lists modulo 3
   bool overlap = false;
   SimArgs ov{};
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t ev_u = nullptr, ev_d = nullptr;
+  cudaStream_t st2 = nullptr, st3 = nullptr;   // deliveries of even and odd steps
+  cudaEvent_t ev_u = nullptr, ev_dk[2] = {nullptr, nullptr};
   std::vector<uint32_t> host_gid_of;      // position -> gid
   std::vector<uint32_t> host_pos_of;      // gid -> position
 };
@@ -933,8 +933,10 @@ int snn_calibrate(snn_ctx* c) {
     c->ov.work_stride = N;
     CK(cudaMemsetAsync(c->ov.n_work, 0, 12, c->st));
     if (!c->st2) CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    if (!c->st3) CK(cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking));
     if (!c->ev_u) CK(cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming));
-    if (!c->ev_d) CK(cudaEventCreateWithFlags(&c->ev_d, cudaEventDisableTiming));
+    for (auto& e : c->ev_dk)
+      if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->overlap = true;
   }
   CK(launch_init_state(s, d_v0, c->st));
@@ -978,15 +980,20 @@ static uint64_t launches_per_batch(snn_ctx* c, uint32_t steps) {
 }
 
 // One rank, overlapped: step_update(PRE) decides the spikes of the first step; then
-// per step k the delivery of step k (stream st2, after the neuron work that listed its
-// spikes) runs beside step_update(k) (stream st, after the delivery of step k - 1,
-// whose slots it reads).  The last step_update takes the input only.
+// per step k the delivery of step k (after the neuron work that listed its spikes) runs
+// beside step_update(k) (stream st, after the delivery of step k - 1, whose slots it
+// reads).  The last step_update takes the input only.  The delivery of step k needs only
+// its list: it writes slots k + d with d >= 1 by commutative reductions, and no later
+// kernel before step_update(k + 1) reads them.  So the deliveries of consecutive steps
+// alternate between two streams and may run at the same time; step_update(k + 1) waits
+// for the delivery of step k.
 // With profile_kernels the same schedule runs (no graph) with a pair of timing events
-// around every launch on its own stream, so each kernel is timed beside the other one as
+// around every launch on its own stream, so each kernel is timed beside the others as
 // in the graph-captured steps.
 static int run_steps_overlapped(snn_ctx* c, uint32_t steps) {
   SimArgs& o = c->ov;
-  cudaStream_t A = c->st, B = c->st2;
+  cudaStream_t A = c->st;
+  cudaStream_t B[2] = {c->st2, c->st3};
   const bool profile = c->cfg.profile_kernels && !c->capturing;
   std::vector<cudaEvent_t> evs;
   if (profile) {
@@ -998,18 +1005,21 @@ static int run_steps_overlapped(snn_ctx* c, uint32_t steps) {
   if (profile) CK(cudaEventRecord(evs[4 * (size_t)steps + 1], A));
   CK(cudaEventRecord(c->ev_u, A));
   for (uint32_t k = 0; k < steps; ++k) {
-    if (k > 0) CK(cudaStreamWaitEvent(A, c->ev_d, 0));
-    CK(cudaStreamWaitEvent(B, c->ev_u, 0));
-    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k], B));
-    CK(launch_deliver(o, k, B, false));
-    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 1], B));
-    CK(cudaEventRecord(c->ev_d, B));
+    cudaStream_t Bk = B[k & 1];
+    if (k > 0) CK(cudaStreamWaitEvent(A, c->ev_dk[(k - 1) & 1], 0));
+    CK(cudaStreamWaitEvent(Bk, c->ev_u, 0));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k], Bk));
+    CK(launch_deliver(o, k, Bk, false));
+    if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 1], Bk));
+    CK(cudaEventRecord(c->ev_dk[k & 1], Bk));
     if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 2], A));
     CK(launch_step_update(o, k, kStepPost | (k + 1 < steps ? kStepPre : 0u), A));
     if (profile) CK(cudaEventRecord(evs[4 * (size_t)k + 3], A));
     CK(cudaEventRecord(c->ev_u, A));
   }
-  CK(cudaStreamWaitEvent(A, c->ev_d, 0));
+  // join both delivery streams (the last step's delivery, and the one before it)
+  CK(cudaStreamWaitEvent(A, c->ev_dk[(steps - 1) & 1], 0));
+  if (steps > 1) CK(cudaStreamWaitEvent(A, c->ev_dk[steps & 1], 0));
   CK(launch_advance(o, steps, A));
   if (profile) {
     CK(cudaStreamSynchronize(A));
@@ -1317,8 +1327,10 @@ void snn_destroy(snn_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   cudaStreamSynchronize(c->st);
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->st3) cudaStreamDestroy(c->st3);
   if (c->ev_u) cudaEventDestroy(c->ev_u);
-  if (c->ev_d) cudaEventDestroy(c->ev_d);
+  for (auto e : c->ev_dk)
+    if (e) cudaEventDestroy(e);
   std::vector<void*> ptrs;
   for (auto& kv : c->live) ptrs.push_back(kv.first);
   for (void* p : ptrs) dfree(c, p);
