@@ -527,6 +527,7 @@ int snn_calibrate(snn_ctx* c) {
                    ? (uint64_t)std::floor(s.rule.param * 4294967296.0) : 0;
     d.cbase = ctot; d.csize = counter_space(s);
     c->cbase[i] = ctot;
+    if (d.csize > ~0ull - ctot) return fail(c, SNN_EINVAL, "counter space of the projections exceeds 64 bits");
     ctot += d.csize;
     d.magic_div = fixed_indegree_shape(s) ? magic_for(d.K) : magic_for(d.n_src);
     d.w_kind = s.w.kind == SNN_W_CONST ? 0 : 1;
