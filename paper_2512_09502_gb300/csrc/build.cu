@@ -89,14 +89,18 @@ __device__ __forceinline__ void gen_items(const BuildArgs& a, const DevBlock& bl
   const uint32_t Kk = (uint32_t)P.K;
   const uint64_t obase = blk.out_base;
   const uint64_t cbase = P.cbase;
+  // the projection's fields in registers: the loop's shared-memory histogram increments
+  // would otherwise make the compiler reload them from the shared copy every item
+  const uint32_t proj_id = P.proj_id, n_src = P.n_src, src_first = P.src_first, src_stride = P.src_stride;
+  const uint32_t d_const = P.d_const, d_len = P.d_tbl_len;
   for (uint32_t i = tid; i < n; i += GEN_BLOCK) {
     const uint64_t e = e0 + i;
     const uint64_t c = FI ? cm + k : e;
-    const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), P.proj_id, kPurposeSynapse), key);
-    const uint32_t si = MODE == GenAll ? k : (MODE == GenOneToOne ? (uint32_t)c : uniform_index(b.x, P.n_src));
-    const uint32_t src = P.src_first + si * P.src_stride;
-    uint32_t d = P.d_const;
-    if (DTAB) d += guided_count(s_tbl, P.d_tbl_len, s_guide, b.y);
+    const uint4 b = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), proj_id, kPurposeSynapse), key);
+    const uint32_t si = MODE == GenAll ? k : (MODE == GenOneToOne ? (uint32_t)c : uniform_index(b.x, n_src));
+    const uint32_t src = src_first + si * src_stride;
+    uint32_t d = d_const;
+    if (DTAB) d += guided_count(s_tbl, d_len, s_guide, b.y);
     if (ONE32) {
       const uint32_t k32 = (src << g.db) | d;
       a.rec_a[obase + e] = ((uint64_t)k32 << g.cbits) | ((cbase + c) & cmask);
