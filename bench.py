@@ -131,9 +131,9 @@ class Clocks:
 # the whole file at capture time, so that a change anywhere in the file, inlined helpers
 # included, retires the figure).
 TRAFFIC = {
-    "gen_kernel": {"bytes_per_unit": 8.02, "source": "build.cu", "file_sha": "95e468867498e6a0"},
-    "onesweep_pass": {"bytes_per_unit": 16.66, "source": "build.cu", "file_sha": "95e468867498e6a0"},
-    "finalize_kernel": {"bytes_per_unit": 17.18, "source": "build.cu", "file_sha": "95e468867498e6a0"},
+    "gen_kernel": {"bytes_per_unit": 8.00, "source": "build.cu", "file_sha": "8215a3e5d3416249"},
+    "onesweep_pass": {"bytes_per_unit": 16.65, "source": "build.cu", "file_sha": "8215a3e5d3416249"},
+    "finalize_kernel": {"bytes_per_unit": 17.19, "source": "build.cu", "file_sha": "8215a3e5d3416249"},
     # steady-state steps 2,000+ of the 500k network, direct-load form (the staged form reads
     # the same bytes); per event of the run's average, per neuron
     "deliver_kernel": {"bytes_per_unit": 11.7, "source": "sim.cu", "file_sha": "9b8df765af2e422e"},
