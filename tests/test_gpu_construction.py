@@ -102,6 +102,19 @@ def test_low_precision_weight_formats(fmt):
     _check(wl.balanced(1001, 250, 37, 9, wl.DELAY_NORMAL, seed=3), fmt)
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_low_precision_weight_formats_over_ranks(fmt):
+    """BF16 and FP16 (power-of-two scale per source) weights on four logical ranks: every
+    rank's layout bit-exact and its weights within the format's rounding of the oracle's,
+    image rows included (their scale is their source's)."""
+    net = wl.balanced(1001, 250, 37, 9, wl.DELAY_NORMAL, seed=4, n_ranks=4)
+    ctx = gpu_build(net, weight_format=fmt)
+    _, ref = oracle_layout(net)
+    for tau in range(4):
+        compare_rank(ctx.get_connections(tau), ref["ranks"][tau], fmt)
+    ctx.destroy()
+
+
 def test_full_size_sampled_parity():
     """The scaled balanced network at full size (5.625G synapses): exact totals, exact
     row sums, and sampled targets regenerated by the oracle found in their source
