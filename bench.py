@@ -146,11 +146,15 @@ def file_sha(path: str) -> str:
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def traffic_of(kernel: str, units_per_launch: float):
+TRAFFIC_WORKLOAD = "balanced_500k"     # the workload every figure above was captured on
+
+
+def traffic_of(kernel: str, units_per_launch: float, workload: str = TRAFFIC_WORKLOAD):
     """Measured DRAM bytes per launch, when the figure was taken on the current text of
-    the kernel's source file; else None."""
+    the kernel's source file and on this workload (bytes per unit differ between
+    workloads: the multi-area ring, for one, is far larger than L2); else None."""
     d = TRAFFIC.get(kernel)
-    if not d:
+    if not d or workload != TRAFFIC_WORKLOAD:
         return None
     src = os.path.join(ROOT, "paper_2512_09502_gb300", "csrc", d["source"])
     if file_sha(src) != d["file_sha"]:
@@ -431,7 +435,7 @@ def run_ours(args):
         table[k] = {"ms_per_launch": v["ms"], "launches_per_step": v["launches"],
                     "share_of_step": v["ms"] * v["launches"] / step_ms, "algorithmic_GBps": gbps,
                     "frac_of_hbm": gbps / peak if gbps else None,
-                    "traffic_bytes_per_launch": traffic_of(k, v["units"])}
+                    "traffic_bytes_per_launch": traffic_of(k, v["units"], args.workload)}
     table["deliver_kernel"]["ms_per_launch_profiled"] = kern["deliver_kernel"]["profiled_ms"]
     table["update_kernel"]["timing"] = "profiled run, events around every launch"
     if net.n_ranks == 1:
@@ -447,7 +451,8 @@ def run_ours(args):
     alg = d["units"] * d["bpu"]
     ach = alg / (d["ms"] / 1000.0) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_kind": peak_kind, "traffic": traffic_of(dom, d["units"]), "algorithmic_bytes_per_launch": alg,
+            "peak_kind": peak_kind, "traffic": traffic_of(dom, d["units"], args.workload),
+            "algorithmic_bytes_per_launch": alg,
             "kernels": table}
 
     cpu = None
