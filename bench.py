@@ -146,6 +146,9 @@ def file_sha(path: str) -> str:
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
+PROBE_STEPS_PER_LAUNCH = 8   # the delivery ceiling probe issues 8 steps' events per launch ...
+PROBE_LAUNCHES = 20          # ... in 20 launches: launch gaps below 1% of the time
+
 TRAFFIC_WORKLOAD = "balanced_500k"     # the workload every figure above was captured on
 
 
@@ -326,7 +329,7 @@ def run_ours(args):
     if args.deliver_mode is not None:
         knobs["deliver_mode"] = args.deliver_mode
 
-    def one(fmt, sim_steps, profile=False):
+    def one(fmt, sim_steps, profile=False, after=None):
         ctx = _lib.build_network(net, weight_format=fmt, allocator=alloc, stream=stream.cuda_stream,
                                  device=local, use_graph=True, profile_kernels=profile, **knobs, **extra)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,6 +339,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         st = ctx.stats()
+        if after is not None:
+            after(ctx, st)
         ctx.destroy()
         return e0.elapsed_time(e1), st
 
@@ -398,8 +403,20 @@ def run_ours(args):
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
     e2e_units, e2e_ms = aggregate(e2e_units, e2e_ms, dist, "cuda")
 
-    # per-kernel CUDA-event times for the roofline (outside the timed region)
-    _, prof = one("f32", min(args.sim_steps, 2000), profile=True)
+    # per-kernel CUDA-event times for the roofline (outside the timed region), and the
+    # delivery's ceiling: the same ring reductions issued by the probe kernel
+    probe = {}
+
+    def run_probe(ctx, st):
+        if net.n_ranks != 1 or not args.sim_steps or not st["n_events"]:
+            return
+        n = int(min(st["n_synapses"], PROBE_STEPS_PER_LAUNCH * st["n_events"] / max(st["steps_done"], 1)))
+        for mode in (0, 1):
+            ctx.ring_reduction_probe(mode, n, 2)                       # warm-up
+            probe[mode] = n / (ctx.ring_reduction_probe(mode, n, PROBE_LAUNCHES) / 1000.0)
+        probe["n"] = n
+
+    _, prof = one("f32", min(args.sim_steps, 2000), profile=True, after=run_probe)
     peak, peak_kind = peaks()
     E = prof["n_synapses"]
     step_ms = ms / args.steps
@@ -454,6 +471,15 @@ def run_ours(args):
             "peak_kind": peak_kind, "traffic": traffic_of(dom, d["units"], args.workload),
             "algorithmic_bytes_per_launch": alg,
             "kernels": table}
+    if probe and dom == "deliver_kernel":
+        dev = d["units"] / (d["ms"] / 1000.0)
+        roof["ceiling"] = {
+            "what": "the delivery's ring reductions replayed by snn_ring_reduction_probe (adds zeros): "
+                    "'streamed' = the direct delivery's loop over consecutive synapses, no spike list; "
+                    "'reductions_only' = the same delays with hashed targets, nothing streamed",
+            "events_per_launch": probe["n"], "launches": PROBE_LAUNCHES,
+            "streamed_events_per_s": probe[0], "reductions_only_events_per_s": probe[1],
+            "deliver_events_per_s": dev, "frac_of_streamed": dev / probe[0], "frac_of_reductions_only": dev / probe[1]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -281,6 +281,25 @@ int snn_stats(snn_ctx* ctx, snn_stats_t* out);
  * bound did not trigger, SNN_ECUDA a CUDA failure.  Allocates 4 KB of device memory. */
 int snn_selftest_bounded_wait(void* cuda_stream);
 
+/* Ceiling probe of the delivery (a measurement of the GPU, no step of the method).  The
+ * delivery of a step adds each event's weight into the target's circular buffer, in the
+ * slot d steps after the current one (App. F, the delivery figure's panel c): ring word
+ * (n + d) mod D.  Its cost is set by these scattered reductions.  The probe
+ * issues `reps` launches of n_events reductions each, at the addresses the delivery uses,
+ * and adds zeros, so the ring keeps its values and a later snn_simulate is unaffected.
+ *   mode 0: the targets, weights and delays of n_events consecutive synapses of the
+ *           layout, streamed exactly as the direct delivery streams a row (weights
+ *           multiplied by zero): the delivery without its spike list and rows;
+ *   mode 1: the delay of the first synapse of every run of 256 and a target drawn
+ *           uniformly from the synapse index by Philox-4x32-10: the reductions alone.
+ * Launch r starts at synapse (r * n_events) mod (E - n_events + 1) and uses ring slot
+ * offset r mod D; the grid is the delivery's.  *ms_per_launch (host) receives the mean
+ * CUDA-event time of one launch on the context's stream (launch gaps included).  One
+ * logical rank, after snn_calibrate (ESTATE before it or in a dry run); EINVAL for another
+ * mode, n_events of 0 or above the synapse count, or reps of 0. */
+int snn_ring_reduction_probe(snn_ctx* ctx, int32_t mode, uint64_t n_events, uint32_t reps,
+                             double* ms_per_launch);
+
 /* ---- allocation-free construction ----------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that cannot
  * call cudaMalloc (a host application that owns all device memory under a fixed

@@ -27,7 +27,8 @@ MAPS = {"R": 0, "L": 1, "S": 2, "T": 3, "P": 4, "TP_PTR": 5, "H": 6, "I": 7, "Q"
 EXPORTED = ["snn_create", "snn_destroy", "snn_last_error", "snn_create_population", "snn_connect",
             "snn_remote_connect", "snn_set_poisson_drive", "snn_calibrate", "snn_simulate",
             "snn_get_spikes", "snn_get_state", "snn_get_connections", "snn_get_row", "snn_get_maps",
-            "snn_get_delay_table", "snn_stats", "snn_selftest_bounded_wait", "snn_connect_sorted_noalloc"]
+            "snn_get_delay_table", "snn_stats", "snn_selftest_bounded_wait", "snn_connect_sorted_noalloc",
+            "snn_ring_reduction_probe"]
 
 
 class SnnError(RuntimeError):
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "snn_get_delay_table": ([ctx, C.c_uint32, C.c_void_p, C.c_uint64, P(C.c_uint64), P(C.c_uint32)], C.c_int),
         "snn_stats": ([ctx, P(snn_stats_t)], C.c_int),
         "snn_selftest_bounded_wait": ([C.c_void_p], C.c_int),
+        "snn_ring_reduction_probe": ([ctx, C.c_int32, C.c_uint64, C.c_uint32, P(C.c_double)], C.c_int),
         "snn_connect_sorted_noalloc": ([C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, P(snn_rule),
                                         P(snn_dist), P(snn_dist), C.c_uint64, C.c_double, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_uint64, P(C.c_uint64), C.c_void_p,
@@ -302,6 +304,13 @@ class Context:
         self._check("snn_get_delay_table", self.lib.snn_get_delay_table(self.h, proj_id, _ptr(buf), n.value,
                                                                         C.byref(n), C.byref(smin)))
         return smin.value, buf
+
+    def ring_reduction_probe(self, mode: int, n_events: int, reps: int) -> float:
+        """Mean ms per launch of the delivery's ceiling probe (snn_ring_reduction_probe)."""
+        ms = C.c_double()
+        self._check("snn_ring_reduction_probe",
+                    self.lib.snn_ring_reduction_probe(self.h, mode, n_events, reps, C.byref(ms)))
+        return ms.value
 
     def stats(self) -> dict:
         s = snn_stats_t()

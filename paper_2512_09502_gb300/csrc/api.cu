@@ -1322,6 +1322,37 @@ int snn_selftest_bounded_wait(void* cuda_stream) {
   return rc;
 }
 
+int snn_ring_reduction_probe(snn_ctx* c, int32_t mode, uint64_t n_events, uint32_t reps, double* ms_per_launch) {
+  if (!c || !ms_per_launch) return SNN_EINVAL;
+  if (!c->calibrated || c->cfg.dry_run) return fail(c, SNN_ESTATE, "the probe needs a calibrated network");
+  if (c->cfg.n_ranks != 1) return fail(c, SNN_EINVAL, "the probe runs on one logical rank");
+  if (mode != 0 && mode != 1) return fail(c, SNN_EINVAL, "probe mode is 0 or 1");
+  if (n_events == 0 || n_events > c->E || reps == 0) return fail(c, SNN_EINVAL, "need 0 < n_events <= synapses, reps > 0");
+  CK(cudaSetDevice(c->cfg.device));
+  const unsigned grid = c->sim.deliver_grid ? c->sim.deliver_grid : (unsigned)c->num_sms * 4u;
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  CK(cudaEventCreate(&e[0]));
+  if (cudaEventCreate(&e[1]) != cudaSuccess) {
+    cudaEventDestroy(e[0]);
+    return fail(c, SNN_ECUDA, "cudaEventCreate");
+  }
+  cudaError_t err = cudaEventRecord(e[0], c->st);
+  for (uint32_t r = 0; r < reps && err == cudaSuccess; ++r) {
+    const uint64_t e0 = ((uint64_t)r * n_events) % (c->E - n_events + 1);
+    err = launch_ring_probe(c->sim, e0, n_events, r % c->ring_slots, (uint32_t)mode, grid, c->st);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e[1], c->st);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e[1]);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e[0], e[1]);
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  if (err != cudaSuccess) return fail(c, SNN_ECUDA, std::string("ring reduction probe: ") + cudaGetErrorString(err));
+  c->stats.kernel_launches += reps;
+  *ms_per_launch = (double)ms / reps;
+  return SNN_OK;
+}
+
 void snn_destroy(snn_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);

@@ -844,6 +844,44 @@ __global__ void __launch_bounds__(TD_BLOCK) deliver_staged_kernel(SimArgs a, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Ceiling probe of the delivery's ring reductions.  It measures the GPU and is no step of
+// the method: every reduction adds a zero (x + 0 = x and x + (-0) = x for every float x), so
+// the ring keeps its values.  Each CTA takes chunks of PROBE_CHUNK consecutive synapses of
+// [e0, e0 + n).  mode 0: deliver_span over the chunk, the direct delivery's loop with the
+// weights multiplied by zero (targets, weights and delays streamed, slot = nb + d).  mode 1:
+// the delay of the first synapse of each run of 256, and a target drawn uniformly by
+// Philox-4x32-10 from the synapse index: nothing but the reductions moves through memory.
+constexpr uint32_t PROBE_CHUNK = 8192;
+
+template <typename WT>
+__global__ void __launch_bounds__(DEL_BLOCK) ring_probe_kernel(SimArgs a, const WT* __restrict__ w, uint64_t e0,
+                                                               uint64_t n, uint32_t nb, uint32_t mode) {
+  const uint64_t pol_stream = policy_evict_first(), pol_ring = policy_evict_last();
+  const uint64_t nchunks = (n + PROBE_CHUNK - 1) / PROBE_CHUNK;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint64_t lo = e0 + c * PROBE_CHUNK;
+    const uint64_t hi = lo + PROBE_CHUNK < e0 + n ? lo + PROBE_CHUNK : e0 + n;
+    if (mode == 0) {
+      deliver_span<WT, DEL_BLOCK>(a, w, nb, lo, hi, threadIdx.x, DEL_BLOCK, 0u, 0.0f, pol_stream, pol_ring);
+      continue;
+    }
+    for (uint64_t b = lo + threadIdx.x; b < hi; b += 4ull * DEL_BLOCK) {
+      const uint4 h = philox_stream(b, 0u, kPurposeProbe, 0ull);
+      const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t e = b + (uint64_t)k * DEL_BLOCK;
+        if (e < hi) {
+          uint32_t slot = nb + __ldg(a.d + (e & ~255ull));
+          if (slot >= a.ring_slots) slot -= a.ring_slots;
+          red_add_keep(a.ring + (uint64_t)slot * a.n_rec * a.ring_stride + uniform_index(hw[k], a.N), 0.0f, pol_ring);
+        }
+      }
+    }
+  }
+}
+
 __global__ void advance_step_kernel(uint32_t* step, uint32_t by) { *step += by; }
 
 __global__ void init_state_kernel(SimArgs a, const float* v0) {
@@ -876,6 +914,15 @@ cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st, b
   if (a.w_format == 0) return launch_deliver_t(a, (const float*)a.w, k_step, st, pdl);
   if (a.w_format == 1) return launch_deliver_t(a, (const __nv_bfloat16*)a.w, k_step, st, pdl);
   return launch_deliver_t(a, (const __half*)a.w, k_step, st, pdl);
+}
+
+cudaError_t launch_ring_probe(const SimArgs& a, uint64_t e0, uint64_t n, uint32_t nb, uint32_t mode, unsigned grid,
+                              cudaStream_t st) {
+  if (a.w_format == 0) ring_probe_kernel<<<grid, DEL_BLOCK, 0, st>>>(a, (const float*)a.w, e0, n, nb, mode);
+  else if (a.w_format == 1)
+    ring_probe_kernel<<<grid, DEL_BLOCK, 0, st>>>(a, (const __nv_bfloat16*)a.w, e0, n, nb, mode);
+  else ring_probe_kernel<<<grid, DEL_BLOCK, 0, st>>>(a, (const __half*)a.w, e0, n, nb, mode);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_update(const SimArgs& a, uint32_t k_step, uint32_t mode, cudaStream_t st) {

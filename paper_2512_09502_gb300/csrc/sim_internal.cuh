@@ -75,5 +75,8 @@ cudaError_t launch_deliver(const SimArgs& a, uint32_t k_step, cudaStream_t st, b
 cudaError_t launch_advance(const SimArgs& a, uint32_t by, cudaStream_t st);
 cudaError_t launch_init_state(const SimArgs& a, const float* v0, cudaStream_t st);
 int staged_deliver_ctas_per_sm(uint32_t w_format);
+// Ceiling probe of the ring reductions (adds zeros; mode 0 streamed layout, mode 1 hashed targets)
+cudaError_t launch_ring_probe(const SimArgs& a, uint64_t e0, uint64_t n, uint32_t nb, uint32_t mode, unsigned grid,
+                              cudaStream_t st);
 
 }  // namespace snn

@@ -23,6 +23,7 @@ constexpr uint32_t kPurposePbTest = 2;
 constexpr uint32_t kPurposePoisson = 3;
 constexpr uint32_t kPurposeVinit = 4;
 constexpr uint32_t kPurposePbGap = 5;
+constexpr uint32_t kPurposeProbe = 6;     // targets of the ring-reduction probe (no step of the method)
 
 constexpr uint32_t kRuleFixedIndegree = 0;
 constexpr uint32_t kRuleFixedTotal = 1;

@@ -236,3 +236,52 @@ def test_network_without_synapses(R):
     assert np.max(np.abs(V - sim.V)) <= 1e-4
     assert ctx.stats()["n_events"] == 0
     ctx.destroy()
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_ring_reduction_probe_leaves_the_simulation_unchanged(fmt):
+    """The delivery's ceiling probe adds zeros at the delivery's ring addresses (streamed
+    layout and hashed targets).  Run between steps it changes nothing: against a context
+    that never ran it, the same spikes, events and membrane potentials, bit for bit (the
+    weights are exact in fp32, so the sums do not depend on the order of the reductions)."""
+    net = _exact_sum_net(2000, 500, 800, 200, R=1)
+    a = gpu_build(net, spike_log_capacity=1 << 20, weight_format=fmt)
+    b = gpu_build(net, spike_log_capacity=1 << 20, weight_format=fmt)
+    a.simulate(100)
+    b.simulate(100)
+    E = a.stats()["n_synapses"]
+    for mode in (0, 1):
+        for n_events in (1, 8191, E // 3, E):          # one event, a ragged chunk, whole layout
+            assert a.ring_reduction_probe(mode, n_events, 3) > 0.0
+    a.simulate(200)
+    b.simulate(200)
+    sa, ga = a.get_spikes()
+    sb, gb = b.get_spikes()
+    assert len(sa) > 100
+    np.testing.assert_array_equal(sa, sb)
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(a.get_state(0, net.n_neurons)[0], b.get_state(0, net.n_neurons)[0])
+    assert a.stats()["n_events"] == b.stats()["n_events"] > 0
+    a.destroy()
+    b.destroy()
+
+
+def test_ring_reduction_probe_rejects_bad_calls():
+    from paper_2512_09502_gb300._lib import SNN_EINVAL, SNN_ESTATE, SnnError, build_network
+    net = _exact_sum_net(400, 100, 40, 10, R=1)
+    ctx = build_network(net)
+    with pytest.raises(SnnError) as ex:                  # before calibrate
+        ctx.ring_reduction_probe(0, 10, 1)
+    assert ex.value.code == SNN_ESTATE
+    ctx.calibrate()
+    E = ctx.stats()["n_synapses"]
+    for mode, n, reps in ((2, 10, 1), (0, 0, 1), (1, E + 1, 1), (0, 10, 0)):
+        with pytest.raises(SnnError) as ex:
+            ctx.ring_reduction_probe(mode, n, reps)
+        assert ex.value.code == SNN_EINVAL
+    ctx.destroy()
+    r2 = gpu_build(_exact_sum_net(400, 100, 40, 10, R=2))
+    with pytest.raises(SnnError) as ex:                  # several logical ranks
+        r2.ring_reduction_probe(0, 10, 1)
+    assert ex.value.code == SNN_EINVAL
+    r2.destroy()
