@@ -136,8 +136,8 @@ TRAFFIC = {
     "finalize_kernel": {"bytes_per_unit": 17.19, "source": "build.cu", "file_sha": "8215a3e5d3416249"},
     # steady-state steps 2,000+ of the 500k network, direct-load form (the staged form reads
     # the same bytes); per event of the run's average, per neuron
-    "deliver_kernel": {"bytes_per_unit": 11.7, "source": "sim.cu", "file_sha": "9b8df765af2e422e"},
-    "update_kernel": {"bytes_per_unit": 10.1, "source": "sim.cu", "file_sha": "9b8df765af2e422e"},
+    "deliver_kernel": {"bytes_per_unit": 11.9, "source": "sim.cu", "file_sha": "c383c5fd5de52ab4"},
+    "update_kernel": {"bytes_per_unit": 10.7, "source": "sim.cu", "file_sha": "c383c5fd5de52ab4"},
 }
 
 
