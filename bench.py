@@ -154,11 +154,43 @@ def file_sha(path: str) -> str:
     return h.hexdigest()[:16]
 
 
+TRAFFIC_WORKLOAD = "balanced_500k"     # the workload the traffic figures were captured on
+
+# Instructions per unit (warp instructions x 32 per record): smsp__inst_executed.sum of a
+# capture of each construction kernel on the 112.5M-synapse balanced case, whose 25-bit
+# (source, delay) key takes the same digit plan (8, 8, 9 bits) as the 500k network; keyed
+# like TRAFFIC.  These kernels are bound by instruction issue, so the bench also reports
+# them against the issue ceiling: SMs x 4 schedulers x 32 lanes x the maximum SM clock.
+INSTR = {
+    "gen_kernel": {"per_unit": 155.0, "source": "build.cu", "file_sha": "a9b78fc905346428"},
+    "onesweep_pass": {"per_unit": (131.4 + 131.4 + 149.1) / 3, "source": "build.cu", "file_sha": "a9b78fc905346428"},
+    "finalize_kernel": {"per_unit": 231.5, "source": "build.cu", "file_sha": "a9b78fc905346428"},
+}
+
+
+def inst_of(kernel: str, workload: str = TRAFFIC_WORKLOAD):
+    """Measured instructions per unit, when taken on the current source and this workload."""
+    d = INSTR.get(kernel)
+    if not d or workload != TRAFFIC_WORKLOAD:
+        return None
+    src = os.path.join(ROOT, "paper_2512_09502_gb300", "csrc", d["source"])
+    return d["per_unit"] if file_sha(src) == d["file_sha"] else None
+
+
+def issue_peak(device: int) -> float:
+    """Thread instructions per second at full issue: SMs x 4 schedulers x 32 lanes x the
+    maximum SM clock (MEASURED_PEAKS.json, else 2,070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return sms * 4 * 32 * mhz * 1e6
+
+
 PROBE_STEPS_PER_LAUNCH = 8   # the delivery ceiling probe issues 8 steps' events per launch ...
 PROBE_LAUNCHES = 20          # ... in 20 launches: launch gaps below 1% of the time
-
-TRAFFIC_WORKLOAD = "balanced_500k"     # the workload every figure above was captured on
-
 
 def traffic_of(kernel: str, units_per_launch: float, workload: str = TRAFFIC_WORKLOAD):
     """Measured DRAM bytes per launch, when the figure was taken on the current text of
@@ -455,12 +487,18 @@ def run_ours(args):
         kern["deliver_kernel"]["ms"] = sim_per_step
         kern["deliver_kernel"]["units"] = s0["n_events"] / args.sim_steps
     table = {}
+    ipk = issue_peak(local)
     for k, v in kern.items():
         gbps = v["units"] * v["bpu"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None
         table[k] = {"ms_per_launch": v["ms"], "launches_per_step": v["launches"],
                     "share_of_step": v["ms"] * v["launches"] / step_ms, "algorithmic_GBps": gbps,
                     "frac_of_hbm": gbps / peak if gbps else None,
                     "traffic_bytes_per_launch": traffic_of(k, v["units"], args.workload)}
+        ipu = inst_of(k, args.workload)
+        if ipu is not None and v["ms"]:
+            table[k]["bound"] = "issue"
+            table[k]["instructions_per_unit"] = ipu
+            table[k]["issue_frac"] = v["units"] * ipu / (v["ms"] / 1000.0) / ipk
     table["deliver_kernel"]["ms_per_launch_profiled"] = kern["deliver_kernel"]["profiled_ms"]
     table["update_kernel"]["timing"] = "profiled run, events around every launch"
     if net.n_ranks == 1:

@@ -67,6 +67,12 @@ def test_traffic_table_names_existing_kernels():
         assert "__global__" in text and (" " + kernel + "(") in text, name
         t = bench.traffic_of(name, 1.0)
         assert (t == d["bytes_per_unit"]) == (bench.file_sha(src) == d["file_sha"]), name
+    for name, d in bench.INSTR.items():           # instruction counts: the same rule
+        src = os.path.join(root, "paper_2512_09502_gb300", "csrc", d["source"])
+        kernel = {"finalize_kernel": "finalize_one_rank_kernel"}.get(name, name)
+        assert (" " + kernel + "(") in open(src).read(), name
+        assert (bench.inst_of(name) == d["per_unit"]) == (bench.file_sha(src) == d["file_sha"]), name
+        assert bench.inst_of(name, "multi_area") is None
 
 
 def test_reference_arm_json_line():
