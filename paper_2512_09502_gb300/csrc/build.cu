@@ -396,7 +396,7 @@ cudaError_t launch_bounded_wait_selftest(uint64_t* status, uint32_t* err, cudaSt
   return cudaGetLastError();
 }
 
-template <int RB, int ITEMS>
+template <int RB, int ITEMS, bool HI>
 __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(BuildArgs a, uint32_t pass,
                                                              const uint64_t* __restrict__ in,
                                                              uint64_t* __restrict__ out,
@@ -423,6 +423,12 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
   const uint32_t n = (uint32_t)min((uint64_t)TILE, seg_end - base);
   const uint32_t shift = a.g.cbits + a.pass_shift[pass];
   const uint64_t dmask = (1ull << a.pass_bits[pass]) - 1;
+  // HI: the digit lies in the record's high word (shift >= 32), so a 32-bit shift of that
+  // word extracts it (the key and counter fit 64 bits); otherwise the 64-bit shift
+  const uint32_t shift_hi = shift - 32;
+  auto digit = [&](uint64_t r) -> uint32_t {
+    return HI ? (((uint32_t)(r >> 32)) >> shift_hi) & (uint32_t)dmask : (uint32_t)((r >> shift) & dmask);
+  };
 
   uint64_t rec[ITEMS];
   uint32_t rnk[ITEMS];
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
-    const uint32_t d = idx < n ? (uint32_t)((rec[j] >> shift) & dmask) : (uint32_t)BINS;
+    const uint32_t d = idx < n ? digit(rec[j]) : (uint32_t)BINS;
     uint32_t peers = 0xffffffffu;
     if ((j & 3) == 3) {
       // every fourth item on the match unit, the rest on ballots: the ballot loop keeps
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     if (idx < n) {
-      const uint32_t d = (uint32_t)((rec[j] >> shift) & dmask);
+      const uint32_t d = digit(rec[j]);
       sm.stage[sm.binstart[d] + sm.whist[warp][d] + rnk[j]] = rec[j];
     }
   }
@@ -557,21 +563,28 @@ __global__ void __launch_bounds__(SORT_BLOCK, SORT_MIN_CTAS) onesweep_pass(Build
   __syncthreads();
   for (uint32_t k = tid; k < n; k += SORT_BLOCK) {
     const uint64_t r = sm.stage[k];
-    const uint32_t d = (uint32_t)((r >> shift) & dmask);
+    const uint32_t d = digit(r);
     const uint64_t gpos = sm.gbase[d] + k;
     if (gpos < seg_end) out[gpos] = r; else atomicOr(a.err, kErrBounds);
   }
 }
 
+template <int RB, int ITEMS, bool HI>
+static cudaError_t sort_pass_hi(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
+                                uint32_t epoch, cudaStream_t st) {
+  const size_t smem = sizeof(SortSmem<RB, ITEMS>);
+  cudaError_t e = cudaFuncSetAttribute(onesweep_pass<RB, ITEMS, HI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  onesweep_pass<RB, ITEMS, HI><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, smem, st>>>(a, pass, in, out, epoch);
+  return cudaGetLastError();
+}
+
 template <int RB, int ITEMS>
 static cudaError_t sort_pass_rb(const BuildArgs& a, uint32_t pass, const uint64_t* in, uint64_t* out,
                                 uint32_t epoch, cudaStream_t st) {
-  const size_t smem = sizeof(SortSmem<RB, ITEMS>);
-  cudaError_t e = cudaFuncSetAttribute(onesweep_pass<RB, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  onesweep_pass<RB, ITEMS><<<(unsigned)a.n_sort_tiles, SORT_BLOCK, smem, st>>>(a, pass, in, out, epoch);
-  return cudaGetLastError();
+  if (a.g.cbits + a.pass_shift[pass] >= 32) return sort_pass_hi<RB, ITEMS, true>(a, pass, in, out, epoch, st);
+  return sort_pass_hi<RB, ITEMS, false>(a, pass, in, out, epoch, st);
 }
 
 bool sort_config_supported(uint32_t radix_bits, uint32_t items) {
